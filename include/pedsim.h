@@ -1,0 +1,239 @@
+/*
+ * pedsim.h - C ABI of the GB300 (sm_103a) bi-directional pedestrian cellular
+ * automaton: the per-timestep update of the Least Effort Model (LEM) and of
+ * the pheromone-guided Ant Colony Optimisation (ACO) variant of Dutta,
+ * McLeod, Friesen, "GPU accelerated Nature Inspired Methods for Modelling
+ * Large Scale Bi-Directional Pedestrian Movement".
+ *
+ * Model (Sec. III): two groups of agents on an H x W grid of cells (W, H
+ * multiples of 16, Sec. IV.a).  Group A starts in the leftmost band_cols
+ * columns and heads for the right edge (+x); group B starts in the rightmost
+ * band_cols columns and heads for the left edge (-x).  Cells outside the grid
+ * are never available.  One step (Sec. IV.b-d) is synchronous: every agent
+ * reads the state at t and proposes a neighbouring empty cell (forward first,
+ * else Eq. 1 for LEM or Eq. 2 for ACO); every empty cell then picks one of the
+ * agents that chose it (scatter-to-gather, no atomics); pheromone evaporates
+ * (Eq. 3) and the movers deposit into their own group's plane (Eq. 4, Eq. 5).
+ * Random numbers come from Philox4x64-10 keyed by (seed, cell, step, stream),
+ * so results depend only on (W, H, params, seed, step count): not on the
+ * stream, the launch shape, the tile shape or the batch a scenario runs in.
+ *
+ * Conventions for every call:
+ *   - return value 0 on success or a negative PEDSIM_E* code; the message of
+ *     the last failure of a handle is returned by sim_last_error() /
+ *     sim_batch_last_error() / sim_pool_last_error();
+ *   - "host" pointers are ordinary CPU memory owned by the caller; "device"
+ *     pointers are CUDA global memory of the current device;
+ *   - calls on one handle are not thread-safe; distinct handles are
+ *     independent.
+ *
+ * Grid layout in memory (all planes row-major, cell c = y * W + x):
+ *   occ   uint8  W*H   0 = empty, 1 = group A agent, 2 = group B agent
+ *   ids   uint32 W*H   agent id 1..2N at occupied cells, 0 at empty cells
+ *   tauA  float  W*H   group A pheromone (ACO only)
+ *   tauB  float  W*H   group B pheromone (ACO only)
+ *   per-agent arrays have 2N+1 entries indexed by id (entry 0 unused):
+ *   arrival uint32     step at which the agent first entered the opposite
+ *                      placement band (0 = not yet), Sec. VI "throughput"
+ *   tour    float      tour length L_k of Eq. 5 (deposit_mode 1)
+ */
+#ifndef PEDSIM_H
+#define PEDSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PEDSIM_OK         0
+#define PEDSIM_EINVAL   (-22)  /* bad argument: sizes, params, NULL handle   */
+#define PEDSIM_ENOMEM   (-12)  /* device or host allocation failed           */
+#define PEDSIM_ENOSPC   (-28)  /* HBM budget of a pool would be exceeded     */
+#define PEDSIM_ECUDA    (-5)   /* a CUDA runtime call failed                 */
+#define PEDSIM_ETIMEDOUT (-110)/* a bounded device wait gave up              */
+#define PEDSIM_ENOENT   (-2)   /* no such scenario / slot                    */
+
+#define PEDSIM_LEM 0u
+#define PEDSIM_ACO 1u
+
+/* Parameters of one scenario.
+ * model        PEDSIM_LEM (Sec. II.A, Eq. 1) or PEDSIM_ACO (Sec. II.B, Eq. 2-5)
+ * n_per_side   agents in each group (N); 0 is allowed (empty grid)
+ * band_cols    width of each placement band; 1 <= band_cols, 2*band_cols <= W,
+ *              n_per_side <= band_cols*H (Sec. III: agents confined to edge
+ *              rows/columns at start)
+ * rho          ACO evaporation rate of Eq. 3, 0 < rho <= 1
+ * tau0         ACO initial pheromone on every cell, >= 0
+ * deposit      ACO constant deposit per visit (deposit_mode 0), >= 0
+ * alpha, beta  ACO exponents of Eq. 2, integers 0..4
+ * deposit_mode 0 = constant `deposit`; 1 = 1/L_k of Eq. 5 with L_k the agent's
+ *              tour length (1 per orthogonal move, fl(sqrt 2) per diagonal)
+ * lem_sigma    standard deviation of the LEM normal rank draw, > 0          */
+typedef struct {
+    uint32_t model;
+    uint32_t n_per_side;
+    uint32_t band_cols;
+    float    rho;
+    float    tau0;
+    float    deposit;
+    uint32_t alpha;
+    uint32_t beta;
+    uint32_t deposit_mode;
+    float    lem_sigma;
+} sim_params;
+
+/* Counters of one scenario.  agents/parked are counted from the grid when
+ * read; crossed, moved and conflicts accumulate from step 0.
+ * agents[g]    agents of group g on the grid (conserved)
+ * crossed[g]   agents of group g that have entered the opposite band (Sec. VI)
+ * parked[g]    agents of group g standing on their goal edge column
+ * moved        total successful moves
+ * conflicts    total (cell, step) pairs where >= 2 agents chose one cell    */
+typedef struct {
+    uint64_t step;
+    uint32_t agents[2];
+    uint32_t crossed[2];
+    uint32_t parked[2];
+    uint64_t moved;
+    uint64_t conflicts;
+} sim_stats_t;
+
+typedef struct sim_s sim_t;
+
+/* Fills *p with the defaults: LEM, N = 0, band 16, rho 0.05, tau0 1,
+ * deposit 1, alpha = beta = 1, deposit_mode 0, lem_sigma 1.                  */
+void sim_default_params(sim_params *p);
+
+/* Checks (W, H, *p) against the rules above; PEDSIM_EINVAL if any fails.   */
+int sim_validate(int W, int H, const sim_params *p);
+
+/* Device bytes one scenario of this size needs (planes, per-agent arrays,
+ * counters); the figure used by pool admission.                              */
+size_t sim_device_bytes(int W, int H, const sim_params *p);
+
+/* Creates a scenario on the current CUDA device and allocates its device
+ * state (owned by the library, freed by sim_destroy).  The grid is empty
+ * until sim_place() or sim_set_state().  *out receives the handle.           */
+int sim_create(int W, int H, const sim_params *p, sim_t **out);
+
+/* Routes all later work of this handle to `stream` (a cudaStream_t, e.g.
+ * torch.cuda.current_stream().cuda_stream); NULL = the legacy default stream.
+ * The library never synchronises the device, only this stream.              */
+int sim_set_stream(sim_t *s, void *stream);
+
+/* Random uniform placement (Sec. IV.a): in each band the n_per_side cells
+ * with the smallest Philox keys (seed, cell, step 0, stream 3) are filled;
+ * group A gets ids 1..N and group B ids N+1..2N in increasing cell index.
+ * Pheromone := tau0, arrival := 0, tour := 0, counters := 0, step := 0.
+ * Asynchronous on the stream.                                                 */
+int sim_place(sim_t *s, uint64_t seed);
+
+/* Advances n >= 0 synchronous steps (Sec. IV.b-d), asynchronously on the
+ * stream.  Long runs replay a captured CUDA graph.                            */
+int sim_step(sim_t *s, int n);
+
+/* Copies the grid at the current step into host buffers (any may be NULL);
+ * ids are 0 at empty cells.  Synchronises the stream.                         */
+int sim_read_grid(sim_t *s, uint8_t *occ, uint32_t *ids, float *tauA, float *tauB);
+
+/* Copies the per-agent arrays (2N+1 entries each, may be NULL) to the host.
+ * Synchronises the stream.                                                    */
+int sim_read_agents(sim_t *s, uint32_t *arrival, float *tour);
+
+/* Replaces the state with a host-provided one (the inputs of an end-to-end
+ * run).  occ/ids must describe 2N agents with ids a permutation of 1..2N,
+ * N = p->n_per_side of sim_create; tauA/tauB/arrival/tour may be NULL (tau0,
+ * zero, zero).  step becomes the step index; counters are reset.  The seed
+ * is the one used by later steps.  Asynchronous (host buffers are staged).   */
+int sim_set_state(sim_t *s, uint64_t seed, uint64_t step, const uint8_t *occ,
+                  const uint32_t *ids, const float *tauA, const float *tauB,
+                  const uint32_t *arrival, const float *tour);
+
+/* Counters at the current step (see sim_stats_t).  Synchronises the stream. */
+int sim_stats(sim_t *s, sim_stats_t *out);
+
+/* Checkpoint: serialises the complete state (params, seed, step, planes,
+ * per-agent arrays, counters).  With buf == NULL, *len receives the size
+ * needed.  sim_load restores a checkpoint written for the same W, H and
+ * params; continuing from it is bit-identical to never having stopped.       */
+int sim_save(sim_t *s, void *buf, size_t *len);
+int sim_load(sim_t *s, const void *buf, size_t len);
+
+/* Selects the step implementation: 0 = fused single pass (default; TMA-
+ * staged tiles, one kernel per step), 1 = two-pass (proposal plane in HBM,
+ * then resolution).  Both give bit-identical results.                         */
+int sim_set_variant(sim_t *s, int variant);
+
+/* Tile shape of the fused pass (tile_w in {32, 64, 128}, tile_h in {8, 16,
+ * 32}) and CTAs per SM of its persistent grid (0 = automatic).               */
+int sim_set_tiling(sim_t *s, int tile_w, int tile_h, int ctas_per_sm);
+
+/* Sticky device error word of the handle: 0, or PEDSIM_ETIMEDOUT when a
+ * bounded device wait gave up.  Synchronises the stream and clears it.       */
+int sim_device_status(sim_t *s);
+
+void sim_destroy(sim_t *s);
+const char *sim_last_error(const sim_t *s);
+
+/* ------------------------------------------------------------------------ */
+/* Batched scenarios: many independent scenarios of uneven size, density and */
+/* model advanced together, each step one persistent launch over all        */
+/* (scenario, tile) work items, the step loop replayed as a CUDA graph.      */
+/* Every scenario's results are bit-identical to running it alone.           */
+/* ------------------------------------------------------------------------ */
+typedef struct batch_s batch_t;
+
+/* Creates n scenarios (W[i], H[i], params[i]) and places each with seeds[i]. */
+int sim_batch_create(int n, const int *W, const int *H, const sim_params *params,
+                     const uint64_t *seeds, batch_t **out);
+int sim_batch_set_stream(batch_t *b, void *stream);
+/* Advances every scenario by n steps (asynchronous).                         */
+int sim_batch_step(batch_t *b, int n);
+/* Counters / grid of scenario i (synchronise the stream).                    */
+int sim_batch_stats(batch_t *b, int i, sim_stats_t *out);
+int sim_batch_read_grid(batch_t *b, int i, uint8_t *occ, uint32_t *ids, float *tauA,
+                        float *tauB);
+/* Tile shape and CTAs per SM of the persistent launch (see sim_set_tiling). */
+int sim_batch_set_tiling(batch_t *b, int tile_w, int tile_h, int ctas_per_sm);
+int sim_batch_device_status(batch_t *b);
+void sim_batch_destroy(batch_t *b);
+const char *sim_batch_last_error(const batch_t *b);
+
+/* ------------------------------------------------------------------------ */
+/* Serving pool: device-resident scenario slots admitted against an HBM      */
+/* budget and stepped together (continuous batching: a slot that finishes   */
+/* frees its memory and a waiting request can be admitted at once).          */
+/* ------------------------------------------------------------------------ */
+typedef struct pool_s pool_t;
+
+/* hbm_budget_bytes bounds the sum of sim_device_bytes() of live slots;
+ * max_slots bounds their number.                                              */
+int sim_pool_create(size_t hbm_budget_bytes, int max_slots, pool_t **out);
+int sim_pool_set_stream(pool_t *pl, void *stream);
+/* Admits one request: allocates its state, places it with `seed` and
+ * schedules `steps` steps.  *slot receives its slot id.  PEDSIM_ENOSPC when
+ * the budget or the slot count would be exceeded (nothing is allocated).     */
+int sim_pool_admit(pool_t *pl, int W, int H, const sim_params *p, uint64_t seed,
+                   uint64_t steps, int *slot);
+/* Advances every live, unfinished slot by up to n steps (a slot stops at its
+ * own step count) in one graph-captured persistent launch per step.          */
+int sim_pool_step(pool_t *pl, int n);
+/* Lists finished slots (synchronises the stream): up to max ids into
+ * done[], their number into *n_done.                                          */
+int sim_pool_finished(pool_t *pl, int *done, int max, int *n_done);
+int sim_pool_stats(pool_t *pl, int slot, sim_stats_t *out);
+int sim_pool_read_grid(pool_t *pl, int slot, uint8_t *occ, uint32_t *ids, float *tauA,
+                       float *tauB);
+/* Frees a slot (finished or not) and its device memory.                       */
+int sim_pool_release(pool_t *pl, int slot);
+size_t sim_pool_bytes_in_use(const pool_t *pl);
+int sim_pool_live(const pool_t *pl);
+void sim_pool_destroy(pool_t *pl);
+const char *sim_pool_last_error(const pool_t *pl);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PEDSIM_H */

@@ -1,0 +1,86 @@
+"""The C-ABI library loads and exports every function include/pedsim.h
+declares; host-only entry points (defaults, validation, sizing) behave as
+documented.  No CUDA compute call is made here."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pedsim.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    names = re.findall(r"\b(sim_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_1412_4933_gb300 import build as B
+    return B.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for core in ("sim_create", "sim_place", "sim_step", "sim_read_grid", "sim_stats",
+                 "sim_save", "sim_load", "sim_destroy", "sim_last_error", "sim_batch_create",
+                 "sim_batch_step", "sim_batch_stats", "sim_pool_admit", "sim_pool_step"):
+        assert core in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = C.CDLL(lib_path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol(lib_path):
+    from paper_1412_4933_gb300 import pedsim as P
+    assert sorted(P.exported_symbols()) == declared_functions()
+
+
+def test_host_only_entry_points(lib_path):
+    from paper_1412_4933_gb300 import pedsim as P
+    p = P.SimParams()
+    P._lib.sim_default_params(C.byref(p))
+    assert (p.model, p.band_cols, p.alpha, p.beta, p.deposit_mode) == (0, 16, 1, 1, 0)
+    assert abs(p.rho - 0.05) < 1e-7 and p.tau0 == 1.0 and p.lem_sigma == 1.0
+    good = P.make_params(model=P.ACO, n_per_side=100, band_cols=8, rho=0.02)
+    assert P.validate(64, 64, good) == P.OK
+    for W, H, prm in [(60, 64, good), (64, 0, good),
+                      (64, 64, P.make_params(model=P.ACO, n_per_side=600, band_cols=8)),
+                      (64, 64, P.make_params(model=P.ACO, n_per_side=10, band_cols=40)),
+                      (64, 64, P.make_params(model=P.ACO, n_per_side=10, band_cols=8, rho=0.0)),
+                      (64, 64, P.make_params(model=P.ACO, n_per_side=10, band_cols=8, beta=7)),
+                      (64, 64, P.make_params(model=3)),
+                      (64, 64, P.make_params(lem_sigma=0.0))]:
+        assert P.validate(W, H, prm) == P.EINVAL
+        assert P.device_bytes(W, H, prm) == 0
+    # ACO 2048^2 with 100K agents: 2 occupancy planes, ids, 4 pheromone planes
+    from paper_1412_4933_gb300 import workloads as WL
+    prm = P.params_of(WL.ACO_2048)
+    nbytes = P.device_bytes(2048, 2048, prm)
+    cells = 2048 * 2048
+    assert 2 * cells + 4 * cells + 16 * cells <= nbytes < 2 * cells + 4 * cells + 16 * cells + 2**20
+    lem = P.params_of(WL.LEM_256)
+    assert P.device_bytes(256, 256, lem) < 7 * 256 * 256
+
+
+def test_oracle_and_library_share_no_source():
+    """The CUDA sources never include or name the oracle and vice versa."""
+    csrc = os.path.join(ROOT, "paper_1412_4933_gb300", "csrc")
+    for f in os.listdir(csrc):
+        text = open(os.path.join(csrc, f)).read()
+        assert "oracle" not in text.lower(), f
+    pkg = os.path.join(ROOT, "paper_1412_4933_gb300")
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            text = open(os.path.join(pkg, f)).read()
+            assert "import oracle" not in text and "from oracle" not in text, f
+    otext = open(os.path.join(ROOT, "oracle", "pedsim_oracle.c")).read()
+    assert "#include \"" not in otext
