@@ -1,0 +1,469 @@
+"""Benchmark of the pedestrian-CA step on GB300.
+
+Headline (one JSON line on rank 0): cell-updates/s of the ACO step on the
+2048x2048 grid with 100K agents (50K per side in 64-column bands, rho 0.02),
+one "step" = one synchronous automaton step (proposal, gather resolution,
+move, evaporation + deposit, counters) over the whole grid, inputs resident
+in HBM.  L2 is flushed (a 512 MB write) between timed steps because the
+scenario's working set (~92 MB) would otherwise stay in the 129 MB L2.
+
+Also reported on the same line:
+  roofline      fused step kernel: algorithmic bytes (18 B/cell) / kernel time
+                vs the measured HBM copy bandwidth
+  cpu_baseline  the single-threaded CPU oracle on a bounded sample
+  e2e           the same metric end to end through the C ABI with host
+                buffers: H2D of the initial state (pinned), the scenario's
+                2000 steps, D2H of the final grid and counters
+  steady        steps replayed back to back (CUDA graph), no flush: the
+                simulation's own L2-resident regime
+  batched       256 uneven scenarios x 500 steps in the persistent batched
+                launch, vs one launch per scenario per step
+  serving       Poisson request stream through the serving pool: p50/p99
+
+`--impl reference` times the CPU oracle instead (the reference arm).
+Under torchrun each rank runs an independent replica (no collective on the
+data path; weak scaling); rank 0 prints the max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1412_4933_gb300 import workloads as WL  # noqa: E402
+
+L2_FLUSH_BYTES = 512 << 20
+ALGO_BYTES_PER_CELL = {WL.LEM: 2, WL.ACO: 18}
+KERNEL_SOURCES = ["paper_1412_4933_gb300/csrc/pedsim_kernels.cu",
+                  "paper_1412_4933_gb300/csrc/pedsim_rules.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_step_aco_2048_traffic.md")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def recorded_traffic():
+    """Per-launch DRAM bytes of the fused kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    try:
+        text = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    src = cur = None
+    for line in text.splitlines():
+        if line.startswith("kernel_source_sha256_16:"):
+            src = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            cur = float(line.split(":", 1)[1].strip())
+    return cur if (src == kernel_source_hash() and cur) else None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self) -> dict:
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl != "reference" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local, dist
+
+
+def max_over_ranks(v: float, dist, device=None) -> float:
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (cpu_baseline leg and reference arm)
+# --------------------------------------------------------------------------
+def oracle_rate(sc, steps: int, warm: int = 0):
+    """Cell-updates/s of the single-threaded oracle over `steps` steps of
+    `sc` after placement and `warm` untimed steps."""
+    from oracle import oracle as O
+    orc = O.Oracle(sc.W, sc.H, O.make_params(**sc.params()), sc.seed)
+    if warm:
+        orc.step(warm)
+    t0 = time.perf_counter()
+    orc.step(steps)
+    dt = time.perf_counter() - t0
+    return sc.cells * steps / dt, dt
+
+
+def run_reference(args, sc):
+    world, rank, local, dist = dist_setup(args)
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    orc = O.Oracle(sc.W, sc.H, O.make_params(**sc.params()), sc.seed)
+    orc.step(args.warmup)
+    t0 = time.perf_counter()
+    orc.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = sc.cells * args.steps / dt
+    line = {
+        "impl": "reference", "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": sc.name, "W": sc.W, "H": sc.H, "agents": sc.agents,
+                   "model": "ACO" if sc.model else "LEM", "rho": sc.rho, "seed": sc.seed,
+                   "l2": "cpu"},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} steps of {sc.name} after {args.warmup} warm-up steps"},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def time_steps_flushed(sim, torch, stream, steps: int, flush):
+    """Sum of per-step CUDA-event times; L2 flushed between steps (outside
+    the events)."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for i in range(steps):
+        flush()
+        evs[i][0].record(stream)
+        sim.step(1)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) * 1e-3 for a, b in evs]
+
+
+def e2e_run(P, torch, sc, stream, reps: int):
+    """End to end through the C ABI from pinned host buffers: set the state,
+    run the scenario's steps, read the final grid and counters back."""
+    cells = sc.cells
+    n = sc.agents
+    # initial state from the library's own placement, staged in pinned memory
+    probe = P.Sim(sc.W, sc.H, P.params_of(sc), stream=stream)
+    probe.place(sc.seed)
+    g0 = probe.read_grid()
+    probe.close()
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
+    h_occ, h_ids = pin(cells, torch.uint8), pin(cells, torch.int32).view(np.uint32)
+    h_ta, h_tb = pin(cells, torch.float32), pin(cells, torch.float32)
+    h_arr = pin(n + 1, torch.int32).view(np.uint32)
+    h_occ[:] = g0["occ"].reshape(-1); h_ids[:] = g0["ids"].reshape(-1)
+    h_ta[:] = g0["tauA"].reshape(-1); h_tb[:] = g0["tauB"].reshape(-1); h_arr[:] = 0
+    o_occ, o_ids = pin(cells, torch.uint8), pin(cells, torch.int32).view(np.uint32)
+    o_ta, o_tb = pin(cells, torch.float32), pin(cells, torch.float32)
+    sim = P.Sim(sc.W, sc.H, P.params_of(sc), stream=stream)
+    aco = sc.model == WL.ACO
+    h2d = cells * (1 + 4) + (8 * cells if aco else 0) + 4 * (n + 1)
+    d2h = cells * (1 + 4) + (8 * cells if aco else 0) + 64
+    times = []
+    for r in range(reps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.set_state(sc.seed, 0, h_occ, h_ids, h_ta if aco else None, h_tb if aco else None, h_arr)
+        sim.step(sc.steps)
+        P._lib.sim_read_grid(sim.handle, P._ptr(o_occ), P._ptr(o_ids),
+                             P._ptr(o_ta) if aco else None, P._ptr(o_tb) if aco else None)
+        st = sim.stats()
+        dt = time.perf_counter() - t0
+        if r > 0:  # first run is warm-up
+            times.append(dt)
+    sim.close()
+    best = statistics.median(times)
+    return {"value": sc.cells * sc.steps / best, "unit": "cell-updates/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "step": f"one {sc.steps}-step run of {sc.name}: H2D of the initial state from pinned "
+                    f"memory, {sc.steps} automaton steps, D2H of the final grid + counters",
+            "seconds_per_run": best, "final_moved": st["moved"]}
+
+
+def batched_leg(P, torch, stream, count=256, steps=500):
+    scs = WL.batched_scenarios(count=count, steps=steps)
+    cells = sum(s.cells for s in scs)
+    batch = P.Batch(scs, stream=stream)
+    batch.step(16)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch.step(steps)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    status = batch.device_status()
+    batch.close()
+    # one launch per scenario per step, same scenarios and steps (a sample of
+    # 32 scenarios, scaled by cells)
+    sample = scs[:32]
+    sims = []
+    for s in sample:
+        sim = P.Sim(s.W, s.H, P.params_of(s), stream=stream)
+        sim.place(s.seed)
+        sims.append(sim)
+    for sim in sims:
+        sim.step(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps // 10):
+        for sim in sims:
+            sim.step(1)
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t0
+    for sim in sims:
+        sim.close()
+    single_rate = sum(s.cells for s in sample) * (steps // 10) / t_single
+    return {"scenarios": count, "steps": steps, "cells": cells,
+            "scenarios_per_s": count / t_batch,
+            "cell_updates_per_s": cells * steps / t_batch,
+            "one_launch_per_scenario_cell_updates_per_s": single_rate,
+            "speedup_vs_one_launch_per_scenario": (cells * steps / t_batch) / single_rate,
+            "device_status": status}
+
+
+def serving_leg(P, torch, stream, n_requests=200, budget_frac=0.5, chunk=16):
+    reqs = WL.serving_requests(n_requests)
+    free, _ = torch.cuda.mem_get_info()
+    pool = P.Pool(int(free * budget_frac), 512, stream=stream)
+    pending = list(reqs)
+    live = {}
+    latencies = []
+    t_start = time.perf_counter()
+    done_cells = 0
+    while pending or live:
+        now = time.perf_counter() - t_start
+        while pending and pending[0].arrival_s <= now:
+            slot = pool.admit(pending[0].scenario)
+            if slot is None:
+                break
+            live[slot] = pending.pop(0)
+        if not live:
+            if pending:
+                time.sleep(max(0.0, pending[0].arrival_s - (time.perf_counter() - t_start)))
+            continue
+        pool.step(chunk)
+        for slot in pool.finished():
+            r = live.pop(slot)
+            latencies.append(time.perf_counter() - t_start - r.arrival_s)
+            done_cells += r.scenario.cells * r.scenario.steps
+            pool.release(slot)
+    total = time.perf_counter() - t_start
+    pool.close()
+    lat = np.array(latencies)
+    return {"requests": n_requests, "rate_per_s": 200.0, "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "scenarios_per_s": n_requests / total,
+            "cell_updates_per_s": done_cells / total, "hbm_budget_frac": budget_frac}
+
+
+def run_gpu(args, sc):
+    import torch
+    world, rank, local, dist = dist_setup(args)
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_1412_4933_gb300 import pedsim as P
+
+    stream = torch.cuda.Stream(device)
+    flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+
+    def flush():
+        with torch.cuda.stream(stream):
+            flush_buf.fill_(1.0)
+
+    with torch.cuda.stream(stream):
+        sim = P.Sim(sc.W, sc.H, P.params_of(sc), stream=stream)
+        sim.place(sc.seed)
+        sim.step(args.warmup)
+    torch.cuda.synchronize()
+    barrier(dist, device)
+
+    with ClockSampler(local) as clk:
+        per_step = time_steps_flushed(sim, torch, stream, args.steps, flush)
+    barrier(dist, device)
+    elapsed = sum(per_step)
+    elapsed_max = max_over_ranks(elapsed, dist, device)
+    clocks = clk.summary()
+    status = sim.device_status()
+
+    cells_total = sc.cells * args.steps * world
+    value = cells_total / elapsed_max
+    ms_per_step = elapsed_max * 1e3 / args.steps
+
+    # roofline of the dominant kernel (fused step): algorithmic bytes / time;
+    # the per-step time also holds the tiny step-index kernel, so this is a
+    # lower bound of the fused kernel's own rate
+    algo_bytes = ALGO_BYTES_PER_CELL[sc.model] * sc.cells
+    peak, peak_kind = measured_peak()
+    step_s = elapsed / args.steps
+    achieved = algo_bytes / step_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": recorded_traffic(),
+                "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes,
+                "kernel": "propose_tile_kernel<16> + resolve_tile_kernel<16>"}
+
+    extra = {}
+    if rank == 0 and not args.quick:
+        # steady state: back-to-back steps (graph replays), no flush
+        with torch.cuda.stream(stream):
+            sim.step(32)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(args.steady_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st_s = e0.elapsed_time(e1) * 1e-3
+        extra["steady"] = {"steps": args.steady_steps, "cell_updates_per_s": sc.cells * args.steady_steps / st_s,
+                           "us_per_step": st_s * 1e6 / args.steady_steps,
+                           "algorithmic_GBps": algo_bytes * args.steady_steps / st_s / 1e9,
+                           "l2": "resident (no flush)"}
+    sim.close()
+
+    e2e = None
+    if rank == 0 and not args.quick:
+        e2e = e2e_run(P, torch, sc, stream, reps=2)
+    if rank == 0 and not args.quick and not args.no_batched:
+        extra["batched"] = batched_leg(P, torch, stream)
+    if rank == 0 and not args.quick and not args.no_serving:
+        extra["serving"] = serving_leg(P, torch, stream)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
+        cpu_steps = args.cpu_steps
+        rate, dt = oracle_rate(sc, cpu_steps)
+        cpu = {"value": rate, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {cpu_steps} steps of {sc.name} after placement "
+                         f"({dt:.1f} s, single-threaded)",
+               "host_cores_available": os.cpu_count()}
+
+    if rank == 0:
+        line = {
+            "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": sc.name, "W": sc.W, "H": sc.H, "agents": sc.agents,
+                       "model": "ACO" if sc.model else "LEM", "rho": sc.rho, "seed": sc.seed,
+                       "band_cols": sc.band_cols, "l2": "flushed between timed steps (512 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clocks, "gpu_launches": 2 * args.steps, "device_status": status,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WL.ACO_2048.name, choices=sorted(WL.SINGLE))
+    ap.add_argument("--steady-steps", type=int, default=2000)
+    ap.add_argument("--cpu-steps", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="headline only (for profiling runs)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    sc = WL.SINGLE[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, sc)
+    return run_gpu(args, sc)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -161,13 +161,27 @@ int sim_stats(sim_t *s, sim_stats_t *out);
 int sim_save(sim_t *s, void *buf, size_t *len);
 int sim_load(sim_t *s, const void *buf, size_t len);
 
-/* Selects the step implementation: 0 = fused single pass (default; TMA-
- * staged tiles, one kernel per step), 1 = two-pass (proposal plane in HBM,
- * then resolution).  Both give bit-identical results.                         */
+/* Step implementations; all give bit-identical results.
+ * PEDSIM_VARIANT_TILED    (default) two kernels per step: TMA-staged
+ *                         proposals of 128 x tile_h tiles into a 1-byte
+ *                         proposal plane, then TMA-staged gather resolution
+ *                         with streamed pheromone evaporation and deposit
+ * PEDSIM_VARIANT_TWO_PASS the same two passes, one thread per cell, plain
+ *                         loads (reference baseline of the tiled kernels)
+ * PEDSIM_VARIANT_FUSED    one persistent kernel per step over TMA-staged
+ *                         tiles with a 3-cell halo (proposals recomputed in
+ *                         the halo instead of a proposal plane)
+ * Selecting a variant resets the tile shape to its default (tiled: 128 x 16;
+ * fused: 64 x 16).                                                            */
+#define PEDSIM_VARIANT_TILED    0
+#define PEDSIM_VARIANT_TWO_PASS 1
+#define PEDSIM_VARIANT_FUSED    2
 int sim_set_variant(sim_t *s, int variant);
 
-/* Tile shape of the fused pass (tile_w in {32, 64, 128}, tile_h in {8, 16,
- * 32}) and CTAs per SM of its persistent grid (0 = automatic).               */
+/* Tile shape of the current variant: tiled: tile_w = 128, tile_h in
+ * {8, 16, 32}; fused: (tile_w, tile_h) in {(32,16), (64,8), (64,16),
+ * (128,8), (128,16)} plus CTAs per SM of its persistent grid (0 =
+ * automatic; ignored by the tiled variant).  PEDSIM_EINVAL otherwise.        */
 int sim_set_tiling(sim_t *s, int tile_w, int tile_h, int ctas_per_sm);
 
 /* Sticky device error word of the handle: 0, or PEDSIM_ETIMEDOUT when a
@@ -195,7 +209,9 @@ int sim_batch_step(batch_t *b, int n);
 int sim_batch_stats(batch_t *b, int i, sim_stats_t *out);
 int sim_batch_read_grid(batch_t *b, int i, uint8_t *occ, uint32_t *ids, float *tauA,
                         float *tauB);
-/* Tile shape and CTAs per SM of the persistent launch (see sim_set_tiling). */
+/* Step variant (PEDSIM_VARIANT_TILED or PEDSIM_VARIANT_FUSED) and tile shape
+ * of the batched launches (see sim_set_variant / sim_set_tiling).            */
+int sim_batch_set_variant(batch_t *b, int variant);
 int sim_batch_set_tiling(batch_t *b, int tile_w, int tile_h, int ctas_per_sm);
 int sim_batch_device_status(batch_t *b);
 void sim_batch_destroy(batch_t *b);

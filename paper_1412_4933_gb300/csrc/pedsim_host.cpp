@@ -24,14 +24,30 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // Device memory layout of one scenario (one allocation)
 // ---------------------------------------------------------------------------
 struct Layout {
-    size_t desc, occ[2], ids, tau[2][2], arrival, tour, counters, step, error, prefix, counts;
+    size_t desc, occ[2], prop, ids, tau[2][2], arrival, tour, part, error, prefix, counts, totals,
+        done;
     size_t total;
+    uint32_t n_slots;
     bool has_tau, has_tour;
 };
+
+int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// Counter slots: one per tile of the smallest tile shape of any variant, and
+// at least one per CTA of the two-pass variant.
+uint32_t counter_slots(int W, int H)
+{
+    int n = ceil_div(W, 32) * ceil_div(H, 16);
+    n = std::max(n, ceil_div(W, 64) * ceil_div(H, 8));
+    n = std::max(n, ceil_div(W, 128) * ceil_div(H, 8));
+    n = std::max(n, two_pass_grid(W, H));
+    return (uint32_t)n;
+}
 
 Layout make_layout(int W, int H, const sim_params &p)
 {
     Layout L{};
+    L.n_slots = counter_slots(W, H);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
@@ -45,16 +61,18 @@ Layout make_layout(int W, int H, const sim_params &p)
     L.desc = take(sizeof(ScenarioDesc));
     L.occ[0] = take(cells);
     L.occ[1] = take(cells);
+    L.prop = take(cells);  // proposal plane of the two-kernel step variants
     L.ids = take(4 * cells);
     for (int g = 0; g < 2; ++g)
         for (int q = 0; q < 2; ++q) L.tau[g][q] = L.has_tau ? take(4 * cells) : 0;
     L.arrival = take(4 * agents);
     L.tour = L.has_tour ? take(4 * agents) : 0;
-    L.counters = take(8 * kNumCounters);
-    L.step = take(8);
+    L.part = take(8 * kNumCounters * (size_t)L.n_slots);
     L.error = take(4);
     L.prefix = take(8);
     L.counts = take(4 * kGridCounts);
+    L.totals = take(8 * kNumCounters);
+    L.done = take(8);  // step ticket and work counter of the fused launch
     L.total = off;
     return L;
 }
@@ -116,16 +134,16 @@ struct sim_s {
     Layout L{};
     uint8_t *dmem = nullptr;
     ScenarioDesc hdesc{};
-    ScenarioDesc *d_desc = nullptr;
+    ScenarioDesc *own_desc = nullptr;  // descriptor in this handle's allocation
+    ScenarioDesc *d_desc = nullptr;    // where the live descriptor is (own or a work list)
     uint32_t *d_prefix = nullptr;
-    uint8_t *d_prop = nullptr;  // two-pass proposal plane (lazy)
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;  // private stream used for graph capture
     unsigned long long step = 0; // host mirror of the device step index
     unsigned long long end_step = ~0ull;
     uint64_t seed = 0;
-    int variant = kVariantFused;
-    int tile_w = 64, tile_h = 16, ctas_per_sm = 0;
+    int variant = kVariantPipeline;
+    int tile_w = 128, tile_h = 16, ctas_per_sm = 0;
     int sms = 1;
     cudaGraphExec_t graph = nullptr;
     cudaStream_t graph_stream = nullptr;
@@ -169,14 +187,16 @@ int upload_desc(sim_t *s)
     const Layout &L = s->L;
     d.occ[0] = m + L.occ[0];
     d.occ[1] = m + L.occ[1];
+    d.prop = m + L.prop;
     d.ids = reinterpret_cast<uint32_t *>(m + L.ids);
     for (int g = 0; g < 2; ++g)
         for (int q = 0; q < 2; ++q)
             d.tau[g][q] = L.has_tau ? reinterpret_cast<float *>(m + L.tau[g][q]) : nullptr;
     d.arrival = reinterpret_cast<uint32_t *>(m + L.arrival);
     d.tour = L.has_tour ? reinterpret_cast<float *>(m + L.tour) : nullptr;
-    d.counters = reinterpret_cast<unsigned long long *>(m + L.counters);
-    d.step = reinterpret_cast<unsigned long long *>(m + L.step);
+    d.part = reinterpret_cast<unsigned long long *>(m + L.part);
+    d.n_slots = L.n_slots;
+    d.step = s->step;
     d.error = reinterpret_cast<int *>(m + L.error);
     d.end_step = s->end_step;
     d.seed = s->seed;
@@ -196,17 +216,41 @@ int upload_desc(sim_t *s)
     d.deposit = s->p.deposit;
     d.lem_scale = 0x1p-16f / s->p.lem_sigma;
     d.tau0 = s->p.tau0;
-    for (int q = 0; q < 2; ++q)
-        if (!encode_2d(&d.map_occ[q], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, d.occ[q], s->W, s->H,
-                       s->tile_w + 32, s->tile_h + 6))
-            return fail(s, PEDSIM_ECUDA, "cuTensorMapEncodeTiled failed (occupancy)");
-    if (L.has_tau)
-        for (int g = 0; g < 2; ++g)
-            for (int q = 0; q < 2; ++q)
-                if (!encode_2d(&d.map_tau[g][q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, d.tau[g][q],
-                               s->W, s->H, s->tile_w, s->tile_h))
-                    return fail(s, PEDSIM_ECUDA, "cuTensorMapEncodeTiled failed (pheromone)");
+    const int TWd = s->tile_w, THd = s->tile_h;
+    if (s->variant == kVariantFused) {
+        for (int q = 0; q < 2; ++q)
+            if (!encode_2d(&d.map_occ[q], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, d.occ[q], s->W, s->H,
+                           s->tile_w + 32, s->tile_h + 6))
+                return fail(s, PEDSIM_ECUDA, "cuTensorMapEncodeTiled failed (occupancy)");
+        if (L.has_tau)
+            for (int g = 0; g < 2; ++g)
+                for (int q = 0; q < 2; ++q)
+                    if (!encode_2d(&d.map_tau[g][q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, d.tau[g][q],
+                                   s->W, s->H, s->tile_w + 8, s->tile_h + 6))
+                        return fail(s, PEDSIM_ECUDA, "cuTensorMapEncodeTiled failed (pheromone)");
+    } else if (s->variant == kVariantPipeline) {
+        bool ok = true;
+        for (int q = 0; q < 2; ++q) {
+            ok = ok && encode_2d(&d.map_occ[q], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, d.occ[q], s->W,
+                                 s->H, TWd + 32, THd + 2);
+            ok = ok && encode_2d(&d.map_occ_out[q], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, d.occ[q],
+                                 s->W, s->H, TWd, THd);
+        }
+        ok = ok && encode_2d(&d.map_prop, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, d.prop, s->W, s->H,
+                             TWd + 32, THd + 4);
+        ok = ok && encode_2d(&d.map_prop_out, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, d.prop, s->W,
+                             s->H, TWd, THd);
+        if (L.has_tau)
+            for (int g = 0; g < 2; ++g)
+                for (int q = 0; q < 2; ++q)
+                    ok = ok && encode_2d(&d.map_tau[g][q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                                         d.tau[g][q], s->W, s->H, TWd, THd);
+        if (!ok) return fail(s, PEDSIM_ECUDA, "cuTensorMapEncodeTiled failed (tiled variant)");
+    }
     const uint32_t prefix[2] = {0u, (uint32_t)(d.tiles_x * d.tiles_y)};
+    // the handle's own descriptor becomes the live one again (a work list that
+    // held it re-uploads its copy when it runs next)
+    s->d_desc = s->own_desc;
     SIM_CUDA(s, cudaMemcpyAsync(s->d_desc, &d, sizeof(d), cudaMemcpyHostToDevice, s->stream));
     // pageable host sources are staged before cudaMemcpyAsync returns
     SIM_CUDA(s, cudaMemcpyAsync(s->d_prefix, prefix, sizeof(prefix), cudaMemcpyHostToDevice,
@@ -222,16 +266,21 @@ int fused_grid(const sim_t *s, uint32_t total)
     return (int)std::max<uint32_t>(1, std::min(total, cap));
 }
 
-// Launches the step kernels of one step with offset t_off on stream st.
+// Launches the kernels of step (step index + t_off) on stream st.
 int launch_one_step(sim_t *s, int t_off, cudaStream_t st)
 {
+    unsigned int *done = reinterpret_cast<unsigned int *>(s->dmem + s->L.done);
+    const uint32_t total = (uint32_t)(s->hdesc.tiles_x * s->hdesc.tiles_y);
     if (s->variant == kVariantTwoPass) {
-        SIM_CUDA(s, launch_two_pass_step(s->d_desc, s->d_prop, s->W, s->H, t_off, st));
+        SIM_CUDA(s, launch_two_pass_step(s->d_desc, s->hdesc.prop, s->W, s->H, t_off, st));
         return PEDSIM_OK;
     }
-    const uint32_t total = (uint32_t)(s->hdesc.tiles_x * s->hdesc.tiles_y);
+    if (s->variant == kVariantPipeline) {
+        SIM_CUDA(s, launch_pipeline_step(s->d_desc, s->d_prefix, 1, total, t_off, s->tile_h, st));
+        return PEDSIM_OK;
+    }
     SIM_CUDA(s, launch_fused_step(s->d_desc, s->d_prefix, 1, total, t_off, s->tile_w, s->tile_h,
-                                  fused_grid(s, total), st));
+                                  fused_grid(s, total), done, st));
     return PEDSIM_OK;
 }
 
@@ -243,17 +292,15 @@ int ensure_graph(sim_t *s)
     SIM_CUDA(s, cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
     int rc = PEDSIM_OK;
     for (int k = 0; k < kGraphSteps && rc == PEDSIM_OK; ++k) rc = launch_one_step(s, k, s->cap);
-    cudaError_t e_adv = cudaSuccess;
-    if (rc == PEDSIM_OK) e_adv = launch_advance(s->d_desc, 1, kGraphSteps, s->cap);
+    if (rc == PEDSIM_OK) {
+        cudaError_t ea = launch_advance(s->d_desc, 1, kGraphSteps, s->cap);
+        if (ea != cudaSuccess) rc = cuda_fail(s, ea, "advance kernel capture");
+    }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(s->cap, &g);
     if (rc != PEDSIM_OK) {
         if (g) cudaGraphDestroy(g);
         return rc;
-    }
-    if (e_adv != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        return cuda_fail(s, e_adv, "advance kernel capture");
     }
     if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamEndCapture");
     e = cudaGraphInstantiate(&s->graph, g, 0);
@@ -309,9 +356,11 @@ static int pedsim_create_on_stream(int W, int H, const sim_params *p, cudaStream
         delete s;
         return e == cudaErrorMemoryAllocation ? PEDSIM_ENOMEM : PEDSIM_ECUDA;
     }
-    s->d_desc = reinterpret_cast<ScenarioDesc *>(s->dmem + s->L.desc);
+    s->own_desc = reinterpret_cast<ScenarioDesc *>(s->dmem + s->L.desc);
+    s->d_desc = s->own_desc;
     s->d_prefix = reinterpret_cast<uint32_t *>(s->dmem + s->L.prefix);
-    if (cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaMemsetAsync(s->dmem + s->L.done, 0, 8, stream) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess) {
         cudaFreeAsync(s->dmem, stream);
         delete s;
         return PEDSIM_ECUDA;
@@ -386,10 +435,6 @@ int sim_step(sim_t *s, int n)
 {
     if (!s || n < 0) return fail(s, PEDSIM_EINVAL, "negative step count");
     if (n == 0) return PEDSIM_OK;
-    if (s->variant == kVariantTwoPass && !s->d_prop) {
-        SIM_CUDA(s, cudaMallocAsync(reinterpret_cast<void **>(&s->d_prop), (size_t)s->W * s->H,
-                                    s->stream));
-    }
     const int full = n / kGraphSteps, rem = n % kGraphSteps;
     if (full > 0) {
         int rc = ensure_graph(s);
@@ -492,9 +537,6 @@ int sim_set_state(sim_t *s, uint64_t seed, uint64_t step, const uint8_t *occ, co
         SIM_CUDA(s, cudaMemcpyAsync(s->hdesc.arrival, arrival, 4 * na, cudaMemcpyHostToDevice, s->stream));
     if (tour && s->L.has_tour)
         SIM_CUDA(s, cudaMemcpyAsync(s->hdesc.tour, tour, 4 * na, cudaMemcpyHostToDevice, s->stream));
-    const unsigned long long st = step;
-    // pageable source: staged before the call returns
-    SIM_CUDA(s, cudaMemcpyAsync(s->hdesc.step, &st, 8, cudaMemcpyHostToDevice, s->stream));
     return PEDSIM_OK;
 }
 
@@ -505,9 +547,11 @@ int sim_stats(sim_t *s, sim_stats_t *out)
     unsigned int counts[kGridCounts];
     const int par = (int)(s->step & 1);
     unsigned int *d_counts = reinterpret_cast<unsigned int *>(s->dmem + s->L.counts);
+    unsigned long long *d_tot = reinterpret_cast<unsigned long long *>(s->dmem + s->L.totals);
     SIM_CUDA(s, launch_grid_counts(s->d_desc, par, s->W * s->H, d_counts, s->stream));
-    SIM_CUDA(s, cudaMemcpyAsync(ctr, s->hdesc.counters, sizeof(ctr), cudaMemcpyDeviceToHost, s->stream));
-    SIM_CUDA(s, cudaMemcpyAsync(&dstep, s->hdesc.step, 8, cudaMemcpyDeviceToHost, s->stream));
+    SIM_CUDA(s, launch_sum_slots(s->d_desc, d_tot, s->stream));
+    SIM_CUDA(s, cudaMemcpyAsync(ctr, d_tot, sizeof(ctr), cudaMemcpyDeviceToHost, s->stream));
+    SIM_CUDA(s, cudaMemcpyAsync(&dstep, &s->d_desc->step, 8, cudaMemcpyDeviceToHost, s->stream));
     SIM_CUDA(s, cudaMemcpyAsync(counts, d_counts, sizeof(counts), cudaMemcpyDeviceToHost, s->stream));
     SIM_CUDA(s, cudaStreamSynchronize(s->stream));
     if (dstep != s->step) return fail(s, PEDSIM_ECUDA, "device step index out of sync");
@@ -579,8 +623,10 @@ int sim_save(sim_t *s, void *buf, size_t *len)
     std::vector<float> tour_tmp(na);
     rc = sim_read_agents(s, arr_tmp.data(), tour_tmp.data());
     if (rc) return rc;
-    SIM_CUDA(s, cudaMemcpyAsync(h.counters, s->hdesc.counters, sizeof(h.counters),
-                                cudaMemcpyDeviceToHost, s->stream));
+    unsigned long long *d_tot = reinterpret_cast<unsigned long long *>(s->dmem + s->L.totals);
+    SIM_CUDA(s, launch_sum_slots(s->d_desc, d_tot, s->stream));
+    SIM_CUDA(s, cudaMemcpyAsync(h.counters, d_tot, sizeof(h.counters), cudaMemcpyDeviceToHost,
+                                s->stream));
     SIM_CUDA(s, cudaStreamSynchronize(s->stream));
     std::memcpy(b, &h, sizeof(h));
     std::memcpy(occ, occ_tmp.data(), cells);
@@ -616,7 +662,8 @@ int sim_load(sim_t *s, const void *buf, size_t len)
     int rc = sim_set_state(s, h.seed, h.step, occ, ids, s->L.has_tau ? tA : nullptr,
                            s->L.has_tau ? tB : nullptr, arr, s->L.has_tour ? tour : nullptr);
     if (rc) return rc;
-    SIM_CUDA(s, cudaMemcpyAsync(s->hdesc.counters, h.counters, sizeof(h.counters),
+    // the saved totals go to slot 0 (sim_set_state cleared every slot)
+    SIM_CUDA(s, cudaMemcpyAsync(s->hdesc.part, h.counters, sizeof(h.counters),
                                 cudaMemcpyHostToDevice, s->stream));
     SIM_CUDA(s, cudaStreamSynchronize(s->stream));
     return PEDSIM_OK;
@@ -624,16 +671,23 @@ int sim_load(sim_t *s, const void *buf, size_t len)
 
 int sim_set_variant(sim_t *s, int variant)
 {
-    if (!s || (variant != kVariantFused && variant != kVariantTwoPass))
+    if (!s || (variant != kVariantPipeline && variant != kVariantTwoPass &&
+               variant != kVariantFused))
         return fail(s, PEDSIM_EINVAL, "unknown variant");
-    if (variant != s->variant) drop_graph(s);
+    if (variant == s->variant) return PEDSIM_OK;
     s->variant = variant;
-    return PEDSIM_OK;
+    // each variant starts from its own default tile shape
+    s->tile_w = variant == kVariantFused ? 64 : 128;
+    s->tile_h = 16;
+    s->ctas_per_sm = 0;
+    return upload_desc(s);
 }
 
 int sim_set_tiling(sim_t *s, int tile_w, int tile_h, int ctas_per_sm)
 {
-    if (!s || !tile_supported(tile_w, tile_h) || ctas_per_sm < 0 || ctas_per_sm > 32)
+    const bool ok = s && (s->variant == kVariantFused ? tile_supported(tile_w, tile_h)
+                                                      : pipeline_tile_supported(tile_w, tile_h));
+    if (!ok || ctas_per_sm < 0 || ctas_per_sm > 32)
         return fail(s, PEDSIM_EINVAL, "unsupported tile shape");
     s->tile_w = tile_w;
     s->tile_h = tile_h;
@@ -659,7 +713,6 @@ void sim_destroy(sim_t *s)
     if (!s) return;
     drop_graph(s);
     // stream-ordered frees: memory returns once the stream's prior work is done
-    if (s->d_prop) cudaFreeAsync(s->d_prop, s->stream);
     if (s->dmem) cudaFreeAsync(s->dmem, s->stream);
     if (s->cap) cudaStreamDestroy(s->cap);
     delete s;
@@ -682,9 +735,11 @@ namespace {
 struct MultiRun {
     ScenarioDesc *d_descs = nullptr;
     uint32_t *d_prefix = nullptr;
+    unsigned int *d_done = nullptr;  // step ticket of the shared launches
     int capacity = 0, count = 0;
     uint32_t total = 0;
-    int tile_w = 64, tile_h = 16, ctas_per_sm = 0, sms = 1;
+    int variant = kVariantPipeline;
+    int tile_w = 128, tile_h = 16, ctas_per_sm = 0, sms = 1;
     cudaStream_t stream = nullptr, cap = nullptr;
     cudaGraphExec_t graph = nullptr;
     std::string err;
@@ -709,6 +764,10 @@ struct MultiRun {
         if (e == cudaSuccess)
             e = cudaMallocAsync(reinterpret_cast<void **>(&d_prefix),
                                 sizeof(uint32_t) * (size_t)(cap_new + 1), stream);
+        if (e == cudaSuccess && !d_done) {
+            e = cudaMallocAsync(reinterpret_cast<void **>(&d_done), 2 * sizeof(unsigned int), stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(d_done, 0, 2 * sizeof(unsigned int), stream);
+        }
         if (e != cudaSuccess) return cuda_(e, "work list allocation");
         capacity = cap_new;
         return PEDSIM_OK;
@@ -727,6 +786,7 @@ struct MultiRun {
         }
         count = (int)sims.size();
         total = pre.back();
+        for (size_t i = 0; i < sims.size(); ++i) h[i].step = sims[i]->step;  // exact host mirror
         if (count) {
             cudaError_t e = cudaMemcpyAsync(d_descs, h.data(), sizeof(ScenarioDesc) * h.size(),
                                             cudaMemcpyHostToDevice, stream);
@@ -735,6 +795,9 @@ struct MultiRun {
                                     cudaMemcpyHostToDevice, stream);
             if (e != cudaSuccess) return cuda_(e, "work list upload");
         }
+        // the array now holds the live descriptors (and step indices) of these
+        // scenarios: every per-scenario call reads them there
+        for (size_t i = 0; i < sims.size(); ++i) sims[i]->d_desc = d_descs + i;
         drop();
         return PEDSIM_OK;
     }
@@ -746,11 +809,14 @@ struct MultiRun {
         return (int)std::max<uint32_t>(1, std::min(total, capn));
     }
 
-    int launch_steps(int k0, int k, cudaStream_t st)
+    int launch_steps(int k, cudaStream_t st)
     {
-        for (int i = k0; i < k0 + k; ++i) {
-            cudaError_t e = launch_fused_step(d_descs, d_prefix, count, total, i, tile_w, tile_h,
-                                              grid(), st);
+        for (int i = 0; i < k; ++i) {
+            cudaError_t e = variant == kVariantFused
+                                ? launch_fused_step(d_descs, d_prefix, count, total, i, tile_w,
+                                                    tile_h, grid(), d_done, st)
+                                : launch_pipeline_step(d_descs, d_prefix, count, total, i, tile_h,
+                                                       st);
             if (e != cudaSuccess) return cuda_(e, "batched step launch");
         }
         cudaError_t e = launch_advance(d_descs, count, k, st);
@@ -762,12 +828,12 @@ struct MultiRun {
     {
         if (n < 0) return fail_(PEDSIM_EINVAL, "negative step count");
         if (n == 0 || count == 0) return PEDSIM_OK;
-        (void)fused_blocks_per_sm(tile_w, tile_h);
+        if (variant == kVariantFused) (void)fused_blocks_per_sm(tile_w, tile_h);
         const int full = n / kGraphSteps, rem = n % kGraphSteps;
         if (full > 0 && !graph) {
             cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
             if (e != cudaSuccess) return cuda_(e, "cudaStreamBeginCapture");
-            int rc = launch_steps(0, kGraphSteps, cap);
+            int rc = launch_steps(kGraphSteps, cap);
             cudaGraph_t g = nullptr;
             e = cudaStreamEndCapture(cap, &g);
             if (rc) { if (g) cudaGraphDestroy(g); return rc; }
@@ -780,7 +846,7 @@ struct MultiRun {
             cudaError_t e = cudaGraphLaunch(graph, stream);
             if (e != cudaSuccess) return cuda_(e, "cudaGraphLaunch");
         }
-        if (rem) return launch_steps(0, rem, stream);
+        if (rem) return launch_steps(rem, stream);
         return PEDSIM_OK;
     }
 
@@ -789,15 +855,18 @@ struct MultiRun {
         drop();
         if (d_descs) cudaFreeAsync(d_descs, stream);
         if (d_prefix) cudaFreeAsync(d_prefix, stream);
+        if (d_done) cudaFreeAsync(d_done, stream);
         d_descs = nullptr;
         d_prefix = nullptr;
+        d_done = nullptr;
         if (cap) cudaStreamDestroy(cap);
         cap = nullptr;
     }
 };
 
-int retile(sim_t *s, int tw, int th, int cps)
+int retile(sim_t *s, int variant, int tw, int th, int cps)
 {
+    s->variant = variant;
     s->tile_w = tw;
     s->tile_h = th;
     s->ctas_per_sm = cps;
@@ -889,15 +958,32 @@ int sim_batch_read_grid(batch_t *b, int i, uint8_t *occ, uint32_t *ids, float *t
 
 int sim_batch_set_tiling(batch_t *b, int tile_w, int tile_h, int ctas_per_sm)
 {
-    if (!b || !tile_supported(tile_w, tile_h) || ctas_per_sm < 0 || ctas_per_sm > 32)
-        return PEDSIM_EINVAL;
+    if (!b) return PEDSIM_EINVAL;
+    const bool ok = b->run.variant == kVariantFused ? tile_supported(tile_w, tile_h)
+                                                    : pipeline_tile_supported(tile_w, tile_h);
+    if (!ok || ctas_per_sm < 0 || ctas_per_sm > 32) return PEDSIM_EINVAL;
     for (sim_t *s : b->sims) {
-        int rc = retile(s, tile_w, tile_h, ctas_per_sm);
+        int rc = retile(s, b->run.variant, tile_w, tile_h, ctas_per_sm);
         if (rc) { b->run.err = s->err; return rc; }
     }
     b->run.tile_w = tile_w;
     b->run.tile_h = tile_h;
     b->run.ctas_per_sm = ctas_per_sm;
+    return b->run.load(b->sims);
+}
+
+int sim_batch_set_variant(batch_t *b, int variant)
+{
+    if (!b || (variant != kVariantPipeline && variant != kVariantFused)) return PEDSIM_EINVAL;
+    b->run.variant = variant;
+    const int tw = variant == kVariantFused ? 64 : 128;
+    for (sim_t *s : b->sims) {
+        int rc = retile(s, variant, tw, 16, 0);
+        if (rc) { b->run.err = s->err; return rc; }
+    }
+    b->run.tile_w = tw;
+    b->run.tile_h = 16;
+    b->run.ctas_per_sm = 0;
     return b->run.load(b->sims);
 }
 
@@ -969,7 +1055,7 @@ int sim_pool_admit(pool_t *pl, int W, int H, const sim_params *p, uint64_t seed,
     int rc = pedsim_create_on_stream(W, H, p, pl->run.stream, &s);
     if (rc) { pl->run.err = "slot creation failed"; return rc; }
     s->end_step = steps;
-    rc = retile(s, pl->run.tile_w, pl->run.tile_h, pl->run.ctas_per_sm);
+    rc = retile(s, pl->run.variant, pl->run.tile_w, pl->run.tile_h, pl->run.ctas_per_sm);
     if (rc == PEDSIM_OK) rc = sim_place(s, seed);
     if (rc) {
         pl->run.err = s->err;
@@ -989,8 +1075,16 @@ int sim_pool_step(pool_t *pl, int n)
     if (!pl || n < 0) return PEDSIM_EINVAL;
     if (pl->dirty) {
         std::vector<sim_t *> live;
-        for (sim_t *s : pl->slots)
-            if (s && s->step < s->end_step) live.push_back(s);
+        for (sim_t *s : pl->slots) {
+            if (!s) continue;
+            if (s->step < s->end_step) {
+                live.push_back(s);
+            } else if (s->d_desc != s->own_desc) {
+                // leaving the work list: its own descriptor becomes live again
+                int rc = upload_desc(s);
+                if (rc) { pl->run.err = s->err; return rc; }
+            }
+        }
         int rc = pl->run.load(live);
         if (rc) return rc;
         pl->dirty = false;

@@ -1,6 +1,7 @@
 // CUDA kernels of the GB300 pedestrian cellular automaton (sm_103a).
 //
-//   init_kernel        clear planes, fill pheromone with tau0, zero arrays
+//   init_kernel        clear planes, fill pheromone with tau0, zero arrays and
+//                      counters
 //   place_kernel       random placement in the edge bands (Sec. IV.a)
 //   fused_step_kernel  one synchronous step (Sec. IV.b-d) in a single pass:
 //                      persistent CTAs walk the (scenario, tile) work list;
@@ -14,8 +15,8 @@
 //   propose_plane_kernel + resolve_plane_kernel
 //                      the same step in two passes through a proposal plane in
 //                      HBM (baseline and cross-check of the fused pass)
-//   advance_kernel     step index += k
-//   grid_counts_kernel / mask_ids_kernel    read-back helpers
+//   grid_counts_kernel agents / parked per group (read-back helper)
+// The last CTA of each step's final kernel advances the step index.
 #include "pedsim_internal.h"
 #include "pedsim_rules.cuh"
 
@@ -81,6 +82,23 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// Shared -> global tiled bulk copy (elements outside the tensor are skipped).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, const void *src)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map),
+        "r"(x), "r"(y), "r"(smem_u32(src))
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// Waits until every committed bulk store has finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read()
+{
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -143,17 +161,20 @@ __device__ __forceinline__ int resolve_cell(const ScenarioDesc &d, int x, int y,
     return (w == 8 - code) ? 0 : o;
 }
 
-__device__ __forceinline__ void flush_counts(const ScenarioDesc &d, Counts &c)
+// Adds the warp's counts to counter slot `slot` of the scenario (warp-shuffle
+// reduction; each tile or CTA owns its slot, so the adds never contend).
+__device__ __forceinline__ void flush_counts(const ScenarioDesc &d, Counts &c, uint32_t slot)
 {
     const unsigned m = __reduce_add_sync(0xffffffffu, c.moved);
     const unsigned k = __reduce_add_sync(0xffffffffu, c.conflicts);
     const unsigned a = __reduce_add_sync(0xffffffffu, c.crossed_a);
     const unsigned b = __reduce_add_sync(0xffffffffu, c.crossed_b);
-    if ((threadIdx.x & 31) == 0) {
-        if (m) atomicAdd(&d.counters[kMoved], (unsigned long long)m);
-        if (k) atomicAdd(&d.counters[kConflicts], (unsigned long long)k);
-        if (a) atomicAdd(&d.counters[kCrossedA], (unsigned long long)a);
-        if (b) atomicAdd(&d.counters[kCrossedB], (unsigned long long)b);
+    if ((threadIdx.x & 31) == 0 && (m | k | a | b)) {
+        unsigned long long *ps = d.part + (size_t)slot * kNumCounters;
+        if (m) atomicAdd(&ps[kMoved], (unsigned long long)m);
+        if (k) atomicAdd(&ps[kConflicts], (unsigned long long)k);
+        if (a) atomicAdd(&ps[kCrossedA], (unsigned long long)a);
+        if (b) atomicAdd(&ps[kCrossedB], (unsigned long long)b);
     }
     c = Counts{};
 }
@@ -179,11 +200,11 @@ __global__ void init_kernel(const ScenarioDesc *__restrict__ descs)
         d.arrival[a] = 0;
         if (d.tour) d.tour[a] = 0.0f;
     }
-    if (blockIdx.x == 0 && threadIdx.x < kNumCounters) d.counters[threadIdx.x] = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *d.step = 0;
-        *d.error = 0;
-    }
+    const size_t slots = (size_t)d.n_slots * kNumCounters;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += stride)
+        d.part[i] = 0;
+    // (the step index is part of the descriptor the host uploads)
+    if (blockIdx.x == 0 && threadIdx.x == 0) *d.error = 0;
 }
 
 // One CTA per (scenario, group): the n band cells with the smallest
@@ -292,22 +313,53 @@ __global__ void __launch_bounds__(1024) place_kernel(const ScenarioDesc *__restr
 
 // ---------------------------------------------------------------------------
 // Fused single-pass step
+//
+// Shared memory of one CTA.  The byte planes use the occupancy tile's column
+// mapping (column cx <-> x = x0 - 16 + cx, row stride OW), so one index
+// arithmetic serves all of them:
+//   occ[stage]     (TH+6) x OW      uint8  TMA copy of rows y0-3 .. y0+TH+2
+//   tau[stage][g]  (TH+6) x (TW+8)  float  TMA copy of x0-4 .. x0+TW+3,
+//                                          rows y0-3 .. y0+TH+2 (ACO)
+//   prop           (TH+4) x OW      uint8  proposal codes, rows y0-2 .. y0+TH+1
+//   win            (TH+2) x OW      uint8  claim masks, then winners, rows
+//                                          y0-1 .. y0+TH
+//   agents         list of the occupied cells of the tile and its 2-ring
+//   moves          list of the tile cells that receive an agent
+//   dep            TH x TW float deposit left in each receiving cell (ACO)
+// A claim mask holds bit j when the neighbour at scan offset j chose the
+// cell; bitwise OR makes it independent of the order claims arrive in.  The
+// winner byte is (scan index + 1) | 0x10 when there were >= 2 claimants.
+// List order never matters: every list entry's effects are independent.
 // ---------------------------------------------------------------------------
+constexpr int kFusedThreads = 128;
+constexpr int align_to(int v, int a) { return (v + a - 1) / a * a; }
+
 template <int TW, int TH>
 struct FusedLayout {
-    static constexpr int OW = TW + 32;        // occupancy tile row, 16-col halo each side
-    static constexpr int OH = TH + 6;         // 3-row halo above and below
-    static constexpr int PW = TW + 4;         // proposal region: tile + 2-cell ring
-    static constexpr int PH = TH + 4;
-    static constexpr int OCC_BYTES = ((OH * OW + 127) / 128) * 128;
-    static constexpr int TAU_BYTES = TH * TW * 4;
-    static constexpr int PROP_BYTES = ((PH * PW + 15) / 16) * 16;
-    static constexpr int OFF_TAU = 2 * OCC_BYTES;                 // [stage][group]
+    static constexpr int OW = TW + 32;
+    static constexpr int OH = TH + 6;
+    static constexpr int TWH = TW + 8;  // pheromone tile row (4-column halo each side)
+    static constexpr int THH = TH + 6;  // 3-row halo above and below
+    static constexpr int OCC_BYTES = align_to(OH * OW, 128);
+    static constexpr int TAU_BOX_BYTES = THH * TWH * 4;
+    static constexpr int TAU_BYTES = align_to(TAU_BOX_BYTES, 128);
+    static constexpr int PROP_BYTES = align_to((TH + 4) * OW, 16);
+    static constexpr int WIN_BYTES = align_to((TH + 2) * OW, 16);
+    static constexpr int MAX_AGENTS = (TH + 4) * (TW + 4);
+    static constexpr int MAX_MOVES = TH * TW;
+    static constexpr int OFF_TAU = 2 * OCC_BYTES;  // [stage][group]
     static constexpr int OFF_PROP = OFF_TAU + 4 * TAU_BYTES;
-    static constexpr int OFF_BAR = OFF_PROP + PROP_BYTES;
-    static constexpr int SMEM = OFF_BAR + 2 * 8 + 128;  // + slack to align the base
-    static_assert(OW <= 256 && OH <= 256 && TW <= 256 && TH <= 256, "TMA box limit");
-    static_assert((TAU_BYTES % 128) == 0, "tau tile alignment");
+    static constexpr int OFF_WIN = OFF_PROP + PROP_BYTES;
+    static constexpr int OFF_DEP = OFF_WIN + WIN_BYTES;
+    static constexpr int OFF_AGENTS = OFF_DEP + TH * TW * 4;
+    static constexpr int OFF_MOVES = OFF_AGENTS + align_to(MAX_AGENTS * 2, 16);
+    static constexpr int OFF_MISC = OFF_MOVES + align_to(MAX_MOVES * 2, 16);  // counters, item
+    static constexpr int OFF_BAR = OFF_MISC + 16;  // misc: 4 words
+    static constexpr int SMEM = OFF_BAR + 16 + 128;  // + slack to align the base
+    // 32-bit word columns covering cx = 12 .. TW+19 (x0-4 .. x0+TW+3)
+    static constexpr int WC0 = 3, NWC = TW / 4 + 2;
+    static_assert(OW <= 256 && OH <= 256 && TWH <= 256 && THH <= 256, "TMA box limit");
+    static_assert((TH + 6) * OW < 65536, "16-bit list entries");
 };
 
 __device__ __forceinline__ int scenario_of(const uint32_t *__restrict__ prefix, int n,
@@ -321,138 +373,714 @@ __device__ __forceinline__ int scenario_of(const uint32_t *__restrict__ prefix, 
     return lo;
 }
 
+// Called by every CTA of the fused kernel as its last action: the last CTA
+// to arrive re-arms the ticket (ctr[0]) and the dynamic work counter (ctr[1])
+// for the next launch.
+__device__ __forceinline__ void finish_launch(unsigned int *ctr)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int ticket = atomicAdd(&ctr[0], 1u);
+        if (ticket == gridDim.x - 1) {
+            atomicExch(&ctr[1], 0u);
+            atomicExch(&ctr[0], 0u);
+            __threadfence();
+        }
+    }
+}
+
+// Per-agent bookkeeping of one move into `cell` from `src` (Sec. IV.d): the
+// id follows the agent, Eq. 5 extends the tour length, the first entry into
+// the opposite band is recorded (Sec. VI).  Returns the deposit's float bits
+// in the low word and 1 << 32 when the agent crossed at this step.
+__device__ __forceinline__ uint64_t apply_move(const ScenarioDesc &d, uint64_t cell,
+                                               uint64_t src, int inc, int xc, bool diagonal,
+                                               uint64_t t)
+{
+    const uint32_t id = d.ids[src];
+    d.ids[cell] = id;
+    float dep = d.deposit;
+    if (d.model == 1 && d.deposit_mode == 1) {
+        const float L = __fadd_rn(d.tour[id], diagonal ? kSqrt2 : 1.0f);
+        d.tour[id] = L;
+        dep = __fdiv_rn(1.0f, L);
+    }
+    uint64_t crossed = 0;
+    const bool in_band = inc == 1 ? xc >= d.W - (int)d.band : xc < (int)d.band;
+    if (in_band && d.arrival[id] == 0) {
+        d.arrival[id] = (uint32_t)(t + 1);
+        crossed = 1ull << 32;
+    }
+    return crossed | (uint64_t)__float_as_uint(dep);
+}
+
 template <int TW, int TH>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kFusedThreads)
 fused_step_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__restrict__ tile_prefix,
-                  int n_scen, uint32_t total, int t_off)
+                  int n_scen, uint32_t total, int t_off, unsigned int *__restrict__ ctr)
 {
     using Lay = FusedLayout<TW, TH>;
-    constexpr int OW = Lay::OW, PW = Lay::PW, PH = Lay::PH;
+    constexpr int NT = kFusedThreads;
+    constexpr int OW = Lay::OW, NWC = Lay::NWC, WC0 = Lay::WC0, TWH = Lay::TWH;
+    constexpr int GW = TW / 4;  // 4-cell groups per tile row
     extern __shared__ __align__(128) uint8_t smem_raw[];
     // TMA destinations need 128-byte alignment: align the base explicitly
     uint8_t *const smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    uint8_t *const occ_s0 = smem;
-    uint8_t *const prop_s = smem + Lay::OFF_PROP;
+    uint8_t *const Pp = smem + Lay::OFF_PROP;
+    uint8_t *const Cw = smem + Lay::OFF_WIN;
+    float *const depv = reinterpret_cast<float *>(smem + Lay::OFF_DEP);
+    uint16_t *const agents = reinterpret_cast<uint16_t *>(smem + Lay::OFF_AGENTS);
+    uint16_t *const moves = reinterpret_cast<uint16_t *>(smem + Lay::OFF_MOVES);
+    unsigned int *const misc = reinterpret_cast<unsigned int *>(smem + Lay::OFF_MISC);
+    // misc[0] agents in the list, misc[1] moves in the list, misc[2] next item
     uint64_t *const bar = reinterpret_cast<uint64_t *>(smem + Lay::OFF_BAR);
     auto occ_stage = [&](int st) { return smem + st * Lay::OCC_BYTES; };
     auto tau_stage = [&](int st, int g) {
         return reinterpret_cast<float *>(smem + Lay::OFF_TAU + (st * 2 + g) * Lay::TAU_BYTES);
     };
-    (void)occ_s0;
 
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbarrier_init();
     }
-    __syncthreads();
 
     // Issues the TMA copies of one work item into a stage (thread 0 only).
     auto issue = [&](uint32_t item, int st) {
         const int s = scenario_of(tile_prefix, n_scen, item);
         const ScenarioDesc *d = descs + s;
-        const uint64_t t = *d->step + (uint64_t)t_off;
+        const uint64_t t = d->step + (uint64_t)t_off;
         if (t >= d->end_step) return;
         const uint32_t local = item - __ldg(tile_prefix + s);
         const int ty = (int)(local / (uint32_t)d->tiles_x), tx = (int)(local % (uint32_t)d->tiles_x);
         const int p = (int)(t & 1);
         const bool aco = d->model == 1;
-        mbar_arrive_expect_tx(&bar[st], Lay::OH * OW + (aco ? 2 * Lay::TAU_BYTES : 0));
+        mbar_arrive_expect_tx(&bar[st], Lay::OH * OW + (aco ? 2 * Lay::TAU_BOX_BYTES : 0));
         tma_load_2d(occ_stage(st), &d->map_occ[p], tx * TW - 16, ty * TH - 3, &bar[st]);
         if (aco) {
-            tma_load_2d(tau_stage(st, 0), &d->map_tau[0][p], tx * TW, ty * TH, &bar[st]);
-            tma_load_2d(tau_stage(st, 1), &d->map_tau[1][p], tx * TW, ty * TH, &bar[st]);
+            tma_load_2d(tau_stage(st, 0), &d->map_tau[0][p], tx * TW - 4, ty * TH - 3, &bar[st]);
+            tma_load_2d(tau_stage(st, 1), &d->map_tau[1][p], tx * TW - 4, ty * TH - 3, &bar[st]);
         }
     };
 
+    // Work items are taken dynamically (ctr[1]) so that tiles crowded with
+    // agents do not pile up on a few CTAs.  Indices are claimed one item
+    // ahead of the prefetch so that the atomic's latency never sits on the
+    // critical path: while item i is computed, item i+1 is being copied and
+    // the index of item i+2 is in flight.
+    if (threadIdx.x == 0) {
+        const uint32_t first = atomicAdd(&ctr[1], 1u);
+        const uint32_t second = atomicAdd(&ctr[1], 1u);
+        misc[2] = first;
+        misc[3] = second;
+        if (first < total) issue(first, 0);
+    }
+    __syncthreads();
+    uint32_t item = misc[2];
+    uint32_t next = misc[3];
+
+    Counts cnt;
     uint32_t phase_bits = 0;
-    uint32_t item = blockIdx.x;
     int st = 0;
-    if (threadIdx.x == 0 && item < total) issue(item, 0);
-    for (; item < total; item += gridDim.x, st ^= 1) {
-        const uint32_t next = item + gridDim.x;
-        if (threadIdx.x == 0 && next < total) {
-            fence_proxy_async_smem();
-            issue(next, st ^ 1);
+    const int lane = threadIdx.x & 31;
+    while (item < total) {
+        uint32_t next2 = 0xFFFFFFFFu;
+        if (threadIdx.x == 0) {
+            misc[0] = 0;
+            misc[1] = 0;
+            if (next < total) {
+                fence_proxy_async_smem();
+                issue(next, st ^ 1);
+                next2 = atomicAdd(&ctr[1], 1u);  // consumed at the end of this item
+            } else {
+                next2 = total;
+            }
         }
+
         const int s = scenario_of(tile_prefix, n_scen, item);
         const ScenarioDesc &d = descs[s];
-        const uint64_t t = *d.step + (uint64_t)t_off;
-        if (t >= d.end_step) continue;  // uniform: nothing was issued for it
-
-        const bool ok = mbar_wait_bounded(&bar[st], (phase_bits >> st) & 1u);
-        phase_bits ^= 1u << st;
+        const uint64_t t = d.step + (uint64_t)t_off;
+        const bool active = t < d.end_step;  // uniform: nothing was issued otherwise
+        bool ok = true;
+        if (active) {
+            ok = mbar_wait_bounded(&bar[st], (phase_bits >> st) & 1u);
+            phase_bits ^= 1u << st;
+        }
         if (!__syncthreads_and(ok)) {
             if (threadIdx.x == 0) atomicExch(d.error, kErrTimeout);
-            // give the copy that may still be in flight for the next item a
-            // bounded chance to land before the CTA exits
+            // give a copy still in flight for the next item a bounded chance to
+            // land before the CTA leaves
             if (next < total) (void)mbar_wait_bounded(&bar[st ^ 1], (phase_bits >> (st ^ 1)) & 1u);
-            return;
+            break;
         }
-
+        if (active) {
         const int W = d.W, H = d.H;
         const uint32_t local = item - __ldg(tile_prefix + s);
         const int ty = (int)(local / (uint32_t)d.tiles_x), tx = (int)(local % (uint32_t)d.tiles_x);
         const int x0 = tx * TW, y0 = ty * TH;
-        const int p = (int)(t & 1);
         const uint8_t *O = occ_stage(st);
-        const RuleParams rp{d.model, d.alpha, d.beta, d.lem_scale};
+        float *tA = tau_stage(st, 0);
+        float *tB = tau_stage(st, 1);
+        const bool aco = d.model == 1;
+        const bool const_deposit = !(aco && d.deposit_mode == 1);
 
-        // Phase 1: proposals of every agent in the tile and a 2-cell ring.
-        for (int i = threadIdx.x; i < PH * PW; i += kThreads) {
-            const int ry = i / PW, rx = i - ry * PW;
-            const int x = x0 - 2 + rx, y = y0 - 2 + ry;
-            int code = 0;
-            if ((unsigned)x < (unsigned)W && (unsigned)y < (unsigned)H) {
-                const int oi = (ry + 1) * OW + (rx + 14);
-                const int g = O[oi];
-                if (g) {
-                    const uint64_t cell = (uint64_t)y * W + x;
-                    const float *tp = d.tau[g - 1 < 2 ? g - 1 : 0][p];
-                    code = propose(
-                        x, y, g, W, H, cell, t, d.seed, rp,
-                        [&](int dx, int dy) { return (int)O[oi + dy * OW + dx]; },
-                        [&](int dx, int dy) { return __ldg(tp + (int64_t)cell + (int64_t)dy * W + dx); });
+        // Phase 0: clear the claim masks; list the agents of the tile and its
+        // 2-ring (cells outside the grid read as empty: TMA zero fill).  A
+        // warp reserves its list slots with one shared atomic.
+        for (int i = threadIdx.x; i < Lay::WIN_BYTES / 16; i += NT)
+            reinterpret_cast<uint4 *>(Cw)[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (int i0 = 0; i0 < (TH + 4) * NWC; i0 += NT) {
+            const int i = i0 + threadIdx.x;
+            uint32_t found = 0;  // bit b: byte b of this word is a listed agent
+            int r = 0, wc = 0;
+            if (i < (TH + 4) * NWC) {
+                r = i / NWC;
+                wc = WC0 + i % NWC;
+                const uint32_t o4 = *reinterpret_cast<const uint32_t *>(O + (r + 1) * OW + 4 * wc);
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int cx = 4 * wc + b;
+                    if (((o4 >> (8 * b)) & 255u) && cx >= 14 && cx <= TW + 17) found |= 1u << b;
                 }
             }
-            prop_s[i] = (uint8_t)code;
+            const int nf = __popc(found);
+            int incl = nf;  // inclusive warp prefix sum of nf
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int warp_total = __shfl_sync(0xffffffffu, incl, 31);
+            unsigned int base = 0;
+            if (lane == 31 && warp_total) base = atomicAdd(&misc[0], (unsigned int)warp_total);
+            base = __shfl_sync(0xffffffffu, base, 31);
+            int slot = (int)base + incl - nf;
+            for (int b = 0; b < 4; ++b)
+                if (found & (1u << b)) agents[slot++] = (uint16_t)((r + 1) * OW + 4 * wc + b);
         }
         __syncthreads();
 
-        // Phase 2: gather, move, evaporate + deposit, count.
-        Counts cnt;
-        const float q = d.q;
-        const bool aco = d.model == 1;
-        const float *tA = tau_stage(st, 0);
-        const float *tB = tau_stage(st, 1);
-        uint8_t *occ_dst = d.occ[p ^ 1];
-        float *tA_dst = d.tau[0][p ^ 1];
-        float *tB_dst = d.tau[1][p ^ 1];
-        for (int i = threadIdx.x; i < TH * TW; i += kThreads) {
-            const int iy = i / TW, ix = i - iy * TW;
-            const int x = x0 + ix, y = y0 + iy;
-            if (x >= W || y >= H) continue;
-            const int oi = (iy + 3) * OW + ix + 16;
-            const int pi = (iy + 2) * PW + ix + 2;
-            const uint64_t cell = (uint64_t)y * W + x;
-            int incoming;
-            float dep;
-            const int no = resolve_cell(
-                d, x, y, cell, t, O[oi], [&](int dx, int dy) { return (int)O[oi + dy * OW + dx]; },
-                [&](int dx, int dy) { return (int)prop_s[pi + dy * PW + dx]; }, cnt, incoming, dep);
-            occ_dst[cell] = (uint8_t)no;
-            if (aco) {
-                float a = __fmul_rn(tA[i], q);
-                float b = __fmul_rn(tB[i], q);
-                if (incoming == 1) a = __fadd_rn(a, dep);
-                else if (incoming == 2) b = __fadd_rn(b, dep);
-                tA_dst[cell] = a;
-                tB_dst[cell] = b;
+        // Phase 1: proposals (Sec. IV.b-c), one agent per thread, from shared
+        // memory only; each proposal that targets the tile or its 1-ring
+        // sets its claim bit there.  Proposal codes are written for occupied
+        // cells only, the only cells whose codes are read.
+        {
+            const RuleParams rp{d.model, d.alpha, d.beta, d.lem_scale};
+            const int n_agents = (int)misc[0];
+            for (int a = threadIdx.x; a < n_agents; a += NT) {
+                const int oi = agents[a];
+                const int r = oi / OW - 1, cx = oi - (oi / OW) * OW;
+                const int x = x0 - 16 + cx, y = y0 - 2 + r;
+                const int g = O[oi];
+                const uint64_t cell = (uint64_t)y * (uint64_t)W + (uint64_t)x;
+                const float *tc = (g == 2 ? tB : tA) + (r + 1) * TWH + (cx - 12);
+                const int code = propose(
+                    x, y, g, W, H, cell, t, d.seed, rp,
+                    [&](int dx, int dy) { return (int)O[oi + dy * OW + dx]; }, tc, TWH);
+                Pp[r * OW + cx] = (uint8_t)code;
+                if (code) {
+                    const int tr = r - 1 + kCodeDY[code];
+                    const int tcx = cx + kCodeDX[code];
+                    if (tr >= 0 && tr < TH + 2 && tcx >= 15 && tcx <= TW + 16) {
+                        const int idx = tr * OW + tcx;
+                        atomicOr(reinterpret_cast<unsigned int *>(Cw + (idx & ~3)),
+                                 (1u << (8 - code)) << (8 * (idx & 3)));
+                    }
+                }
             }
         }
-        flush_counts(d, cnt);
         __syncthreads();
+
+        // Phase 1c: one winner per claimed cell of the tile and its 1-ring
+        // (Sec. IV.d): the only claimant, or claimant floor(r * k / 2^32) in
+        // scan order from Philox stream 2 at the target cell.  Tile cells
+        // that receive an agent go to the move list.
+        for (int i0 = 0; i0 < (TH + 2) * NWC; i0 += NT) {
+            const int i = i0 + threadIdx.x;
+            uint32_t into = 0;  // bit b: byte b is a tile cell receiving an agent
+            int r = 0, wc = 0;
+            if (i < (TH + 2) * NWC) {
+                r = i / NWC;
+                wc = WC0 + i % NWC;
+                uint32_t *cp = reinterpret_cast<uint32_t *>(Cw + r * OW + 4 * wc);
+                const uint32_t m4 = *cp;
+                if (m4) {
+                    uint32_t w4 = 0;
+                    for (int b = 0; b < 4; ++b) {
+                        const uint32_t m = (m4 >> (8 * b)) & 255u;
+                        if (!m) continue;
+                        const uint32_t k = (uint32_t)__popc(m);
+                        const int cx = 4 * wc + b;
+                        uint32_t j;
+                        if (k == 1) {
+                            j = (uint32_t)(__ffs(m) - 1);
+                        } else {
+                            const int x = x0 - 16 + cx, y = y0 - 1 + r;
+                            j = pick_claimant(m, k, (uint64_t)y * (uint64_t)W + (uint64_t)x, t, d.seed);
+                        }
+                        w4 |= ((j + 1u) | (k >= 2 ? 0x10u : 0u)) << (8 * b);
+                        if (r >= 1 && r <= TH && cx >= 16 && cx < TW + 16) into |= 1u << b;
+                    }
+                    *cp = w4;
+                }
+            }
+            const int nf = __popc(into);
+            int incl = nf;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int warp_total = __shfl_sync(0xffffffffu, incl, 31);
+            unsigned int base = 0;
+            if (lane == 31 && warp_total) base = atomicAdd(&misc[1], (unsigned int)warp_total);
+            base = __shfl_sync(0xffffffffu, base, 31);
+            int slot = (int)base + incl - nf;
+            for (int b = 0; b < 4; ++b)
+                if (into & (1u << b)) moves[slot++] = (uint16_t)((r - 1) * TW + 4 * wc + b - 16);
+        }
+        __syncthreads();
+
+        // Phase 2a: per-agent bookkeeping of the moves into tile cells (ids,
+        // tour length, arrival), one move per thread.  With a constant
+        // deposit nothing below depends on it, so the dense pass starts at
+        // once and hides these global round trips; with Eq. 5 the deposits
+        // go to shared memory first.
+        {
+            const int n_moves = (int)misc[1];
+            for (int mi = threadIdx.x; mi < n_moves; mi += NT) {
+                const int li = moves[mi];
+                const int iy = li / TW, ix = li - iy * TW;
+                const int x = x0 + ix, y = y0 + iy;
+                const int w = Cw[(iy + 1) * OW + ix + 16];
+                const int j = (w & 15) - 1;
+                const int dx = kCodeDX[j + 1], dy = kCodeDY[j + 1];
+                const int inc = O[(iy + 3 + dy) * OW + ix + 16 + dx];
+                const uint64_t cell = (uint64_t)y * (uint64_t)W + (uint64_t)x;
+                const uint64_t rv = apply_move(d, cell, cell + (int64_t)dy * W + dx, inc, x,
+                                               dx != 0 && dy != 0, t);
+                ++cnt.moved;
+                cnt.conflicts += (w >> 4) & 1;
+                const unsigned crossed = (unsigned)(rv >> 32);
+                if (inc == 1) cnt.crossed_a += crossed; else cnt.crossed_b += crossed;
+                if (!const_deposit) depv[li] = __uint_as_float((uint32_t)rv);
+            }
+        }
+        if (!const_deposit) __syncthreads();
+
+        // Phase 2b: per group of 4 tile cells: the winner's group enters each
+        // empty cell, cells whose agent won are vacated, pheromone evaporates
+        // (Eq. 3) and the deposit lands in the mover's own plane (Eq. 4).
+        {
+            const int p = (int)(t & 1);
+            const float q = d.q;
+            const float dep0 = d.deposit;
+            uint8_t *occ_dst = d.occ[p ^ 1];
+            float *tA_dst = d.tau[0][p ^ 1];
+            float *tB_dst = d.tau[1][p ^ 1];
+            for (int gi = threadIdx.x; gi < TH * GW; gi += NT) {
+                const int iy = gi / GW, gx = gi - iy * GW;
+                const int x = x0 + 4 * gx, y = y0 + iy;
+                if (x >= W || y >= H) continue;
+                const int cxo = 16 + 4 * gx;
+                const uint32_t o4 = *reinterpret_cast<const uint32_t *>(O + (iy + 3) * OW + cxo);
+                const uint32_t w4 = *reinterpret_cast<const uint32_t *>(Cw + (iy + 1) * OW + cxo);
+                const uint64_t cell0 = (uint64_t)y * (uint64_t)W + (uint64_t)x;
+                float va[4], vb[4];
+                if (aco) {
+                    const int ti = (iy + 3) * TWH + 4 * gx + 4;
+                    const float4 a4 = *reinterpret_cast<const float4 *>(tA + ti);
+                    const float4 b4 = *reinterpret_cast<const float4 *>(tB + ti);
+                    va[0] = __fmul_rn(a4.x, q); va[1] = __fmul_rn(a4.y, q);
+                    va[2] = __fmul_rn(a4.z, q); va[3] = __fmul_rn(a4.w, q);
+                    vb[0] = __fmul_rn(b4.x, q); vb[1] = __fmul_rn(b4.y, q);
+                    vb[2] = __fmul_rn(b4.z, q); vb[3] = __fmul_rn(b4.w, q);
+                }
+                uint32_t n4 = o4;
+                if (o4 | w4) {
+                    const uint32_t p4 = *reinterpret_cast<const uint32_t *>(Pp + (iy + 2) * OW + cxo);
+                    n4 = 0;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int o = (o4 >> (8 * b)) & 255u;
+                        int no = o;
+                        if (o == 0) {
+                            const int w = (w4 >> (8 * b)) & 255u;
+                            if (w) {
+                                const int j = (w & 15) - 1;
+                                no = O[(iy + 3 + kCodeDY[j + 1]) * OW + cxo + b + kCodeDX[j + 1]];
+                                if (aco) {
+                                    const float dep = const_deposit ? dep0 : depv[iy * TW + 4 * gx + b];
+                                    if (no == 1) va[b] = __fadd_rn(va[b], dep);
+                                    else vb[b] = __fadd_rn(vb[b], dep);
+                                }
+                            }
+                        } else {
+                            const int code = (p4 >> (8 * b)) & 255u;
+                            if (code) {
+                                const int wt = Cw[(iy + 1 + kCodeDY[code]) * OW + cxo + b + kCodeDX[code]];
+                                if ((wt & 15) == 9 - code) no = 0;  // this agent won its target
+                            }
+                        }
+                        n4 |= (uint32_t)no << (8 * b);
+                    }
+                }
+                *reinterpret_cast<uint32_t *>(occ_dst + cell0) = n4;
+                if (aco) {
+                    *reinterpret_cast<float4 *>(tA_dst + cell0) = make_float4(va[0], va[1], va[2], va[3]);
+                    *reinterpret_cast<float4 *>(tB_dst + cell0) = make_float4(vb[0], vb[1], vb[2], vb[3]);
+                }
+            }
+        }
+            flush_counts(d, cnt, local);
+        }  // active
+        // publish the index claimed above; every thread is done with this item
+        if (threadIdx.x == 0) misc[2] = next2;
+        __syncthreads();
+        item = next;
+        next = misc[2];
+        st ^= 1;
     }
+    finish_launch(ctr);
+}
+
+// ---------------------------------------------------------------------------
+// Tiled two-kernel step (the default variant)
+//
+// K1 propose_tile_kernel: one CTA per 128 x TH tile; TMA stages the tile's
+// occupancy with a 1-cell halo (16 columns either side for the 16-byte rule);
+// each thread owns 16 consecutive cells of a row and writes their proposal
+// codes to the proposal plane with one 16-byte store.
+// K2 resolve_tile_kernel: one CTA per tile; TMA stages the proposal plane with
+// a 2-cell halo and the occupancy with a 1-cell halo while each thread's
+// pheromone loads (4 x float4 per plane) are already in flight.  Pheromone
+// evaporates (Eq. 3) and is stored at once; a 3 x 18 window test on the
+// proposals sends every 16-cell segment with no nearby proposal down a fast
+// path (occupancy unchanged); otherwise each empty cell gathers its winner
+// (Sec. IV.d) and each agent checks whether it won its target.  A move
+// overwrites the one pheromone value that receives a deposit (Eq. 4/5).
+// ---------------------------------------------------------------------------
+constexpr int kPipeTileW = 128;
+constexpr int kPipeRowB = kPipeTileW + 32;  // staged row: 16-column halo either side
+
+// Appends `n` entries of this thread to a shared list with one shared atomic
+// per warp; returns the first slot of this thread.  All 32 lanes must call.
+__device__ __forceinline__ int warp_reserve(unsigned int *counter, int n)
+{
+    const int lane = threadIdx.x & 31;
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned int base = 0;
+    if (lane == 31 && total) base = atomicAdd(counter, (unsigned int)total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return (int)base + incl - n;
+}
+
+// Forward-first part of a proposal (Sec. III): 0 for an agent on its goal
+// column, the forward code when the forward cell is in the grid and empty,
+// -1 when the agent is blocked and needs the full rule.
+template <class OccFn>
+__device__ __forceinline__ int forward_first(int x, int y, int g, int W, int H, OccFn occ)
+{
+    if ((g == 1 && x == W - 1) || (g == 2 && x == 0)) return 0;
+    const int code = kFrameCode[g - 1][1];
+    const int dx = kCodeDX[code];
+    const int nx = x + dx;
+    if ((unsigned)nx < (unsigned)W && occ(dx, 0) == 0) return code;
+    (void)y;
+    (void)H;
+    return -1;
+}
+
+// Copies a scenario's descriptor header into shared memory (16 bytes per
+// thread of the first 16 threads); the caller synchronises.
+__device__ __forceinline__ void load_header(ScenarioDesc *dst, const ScenarioDesc *src)
+{
+    if (threadIdx.x < kDescHeaderBytes / 16)
+        reinterpret_cast<uint4 *>(dst)[threadIdx.x] =
+            __ldg(reinterpret_cast<const uint4 *>(src) + threadIdx.x);
+}
+
+template <int TH>
+__global__ void __launch_bounds__(8 * TH)
+propose_tile_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__restrict__ tile_prefix,
+                    int n_scen, int t_off)
+{
+    constexpr int NT = 8 * TH, RB = kPipeRowB, TW = kPipeTileW;
+    __shared__ __align__(128) uint8_t occ_s[(TH + 2) * RB];
+    __shared__ __align__(128) uint8_t code_s[TH * TW];
+    __shared__ __align__(128) ScenarioDesc hdr_s;  // header part only
+    __shared__ uint16_t blocked[TH * TW];
+    __shared__ unsigned int n_blocked;
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t item = blockIdx.x;
+    const int s = scenario_of(tile_prefix, n_scen, item);
+    const ScenarioDesc *gd = descs + s;
+    load_header(&hdr_s, gd);
+    __syncthreads();
+    const ScenarioDesc &d = hdr_s;
+    const uint64_t t = d.step + (uint64_t)t_off;
+    if (t >= d.end_step) return;
+    const uint32_t local = item - __ldg(tile_prefix + s);
+    const int ty = (int)(local / (uint32_t)d.tiles_x), tx = (int)(local % (uint32_t)d.tiles_x);
+    const int x0 = tx * TW, y0 = ty * TH;
+    const int p = (int)(t & 1);
+    if (threadIdx.x == 0) {
+        n_blocked = 0;
+        mbar_init(&bar, 1);
+        fence_mbarrier_init();
+        mbar_arrive_expect_tx(&bar, (TH + 2) * RB);
+        tma_load_2d(occ_s, &gd->map_occ[p], x0 - 16, y0 - 1, &bar);
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0);
+    if (!__syncthreads_and(ok)) {
+        if (threadIdx.x == 0) atomicExch(d.error, kErrTimeout);
+        return;
+    }
+    const int W = d.W, H = d.H;
+    const int r = threadIdx.x >> 3, seg = threadIdx.x & 7;
+    const int y = y0 + r, x = x0 + 16 * seg;
+    const int c0 = (r + 1) * RB + 16 + 16 * seg;
+
+    // Pass 1 (owner thread): forward-first codes; blocked agents are listed.
+    uint32_t blocked_mask = 0;
+    uint4 codes = make_uint4(0u, 0u, 0u, 0u);
+    const uint4 o = *reinterpret_cast<const uint4 *>(occ_s + c0);  // zero outside the grid
+    if (o.x | o.y | o.z | o.w) {
+        uint64_t lo = 0, hi = 0;
+#pragma unroll 4
+        for (int b = 0; b < 16; ++b) {
+            const int g = occ_s[c0 + b];
+            if (!g) continue;
+            const int code = forward_first(x + b, y, g, W, H,
+                                           [&](int dx, int dy) { return (int)occ_s[c0 + b + dy * RB + dx]; });
+            if (code < 0) { blocked_mask |= 1u << b; continue; }
+            if (b < 8) lo |= (uint64_t)code << (8 * b);
+            else hi |= (uint64_t)code << (8 * (b - 8));
+        }
+        codes = make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
+    }
+    *reinterpret_cast<uint4 *>(code_s + r * TW + 16 * seg) = codes;
+    int slot = warp_reserve(&n_blocked, __popc(blocked_mask));
+    while (blocked_mask) {
+        const int b = __ffs(blocked_mask) - 1;
+        blocked_mask &= blocked_mask - 1;
+        blocked[slot++] = (uint16_t)(r * TW + 16 * seg + b);
+    }
+    __syncthreads();
+
+    // Pass 2: the full rule for blocked agents, one agent per thread.
+    {
+        const RuleParams rp{d.model, d.alpha, d.beta, d.lem_scale};
+        const int nb = (int)n_blocked;
+        for (int i = threadIdx.x; i < nb; i += NT) {
+            const int li = blocked[i];
+            const int ly = li / TW, lx = li - ly * TW;
+            const int xc = x0 + lx, yc = y0 + ly;
+            const int oi = (ly + 1) * RB + 16 + lx;
+            const int g = occ_s[oi];
+            const uint64_t cell = (uint64_t)yc * (uint64_t)W + (uint64_t)xc;
+            const float *tp = d.tau[g == 2 ? 1 : 0][p];
+            code_s[li] = (uint8_t)propose(
+                xc, yc, g, W, H, cell, t, d.seed, rp,
+                [&](int dx, int dy) { return (int)occ_s[oi + dy * RB + dx]; },
+                tp ? tp + cell : nullptr, W);
+        }
+    }
+    // The tile of codes leaves by one TMA store (cells outside the grid are
+    // skipped by the copy).
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tma_store_2d(&gd->map_prop_out, x0, y0, code_s);
+        bulk_commit();
+        bulk_wait_read();
+    }
+}
+
+template <int TH>
+__global__ void __launch_bounds__(8 * TH)
+resolve_tile_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__restrict__ tile_prefix,
+                    int n_scen, int t_off)
+{
+    constexpr int NT = 8 * TH, RB = kPipeRowB, TW = kPipeTileW;
+    constexpr int NWC = TW / 4 + 2;  // 32-bit word columns covering x0-4 .. x0+TW+3
+    __shared__ __align__(128) float tau_s[2][TH * TW];
+    __shared__ __align__(128) uint8_t prop_s[(TH + 4) * RB];  // rows y0-2 .. y0+TH+1
+    __shared__ __align__(128) uint8_t occ_s[(TH + 2) * RB];   // rows y0-1 .. y0+TH
+    __shared__ __align__(128) uint8_t win_s[(TH + 2) * RB];   // claim masks, then winners
+    __shared__ __align__(128) uint8_t occn_s[TH * TW];
+    __shared__ __align__(128) ScenarioDesc hdr_s;  // header part only
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t item = blockIdx.x;
+    const int s = scenario_of(tile_prefix, n_scen, item);
+    const ScenarioDesc *gd = descs + s;
+    load_header(&hdr_s, gd);
+    // claim masks start at zero
+    for (int i = threadIdx.x; i < (TH + 2) * RB / 16; i += NT)
+        reinterpret_cast<uint4 *>(win_s)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    const ScenarioDesc &d = hdr_s;
+    const uint64_t t = d.step + (uint64_t)t_off;
+    Counts cnt;
+    if (t < d.end_step) {
+        const uint32_t local = item - __ldg(tile_prefix + s);
+        const int ty = (int)(local / (uint32_t)d.tiles_x), tx = (int)(local % (uint32_t)d.tiles_x);
+        const int x0 = tx * TW, y0 = ty * TH;
+        const int p = (int)(t & 1);
+        const bool aco = d.model == 1;
+        if (threadIdx.x == 0) {
+            mbar_init(&bar, 1);
+            fence_mbarrier_init();
+            mbar_arrive_expect_tx(&bar, (TH + 4) * RB + (TH + 2) * RB + (aco ? 2 * TH * TW * 4 : 0));
+            tma_load_2d(prop_s, &gd->map_prop, x0 - 16, y0 - 2, &bar);
+            tma_load_2d(occ_s, &gd->map_occ[p], x0 - 16, y0 - 1, &bar);
+            if (aco) {
+                tma_load_2d(tau_s[0], &gd->map_tau[0][p], x0, y0, &bar);
+                tma_load_2d(tau_s[1], &gd->map_tau[1][p], x0, y0, &bar);
+            }
+        }
+        const int W = d.W, H = d.H;
+        __syncthreads();  // barrier initialised
+        const bool ok = mbar_wait_bounded(&bar, 0);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) atomicExch(d.error, kErrTimeout);
+        } else {
+            // Claim pass: every proposal of the tile and its 2-ring that targets
+            // the tile or its 1-ring sets bit (8 - code) of the target's mask
+            // (the claimant's scan offset seen from the target).  Cells outside
+            // the grid hold no proposal (TMA zero fill).
+            for (int i = threadIdx.x; i < (TH + 4) * NWC; i += NT) {
+                const int r = i / NWC, wc = 3 + i % NWC;
+                const uint32_t p4 = *reinterpret_cast<const uint32_t *>(prop_s + r * RB + 4 * wc);
+                if (!p4) continue;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int code = (p4 >> (8 * b)) & 255u;
+                    const int cx = 4 * wc + b;
+                    if (!code || cx < 14 || cx > TW + 17) continue;
+                    const int tr = r - 1 + kCodeDY[code];  // target row in win_s
+                    const int tc = cx + kCodeDX[code];
+                    if (tr >= 0 && tr < TH + 2 && tc >= 15 && tc <= TW + 16) {
+                        const int idx = tr * RB + tc;
+                        atomicOr(reinterpret_cast<unsigned int *>(win_s + (idx & ~3)),
+                                 (1u << (8 - code)) << (8 * (idx & 3)));
+                    }
+                }
+            }
+            __syncthreads();
+
+            // Winner pass (Sec. IV.d): the only claimant, or claimant
+            // floor(r * k / 2^32) in scan order from Philox stream 2 at the
+            // target cell; the byte becomes (scan index + 1) | 0x10 if k >= 2.
+            for (int i = threadIdx.x; i < (TH + 2) * NWC; i += NT) {
+                const int r = i / NWC, wc = 3 + i % NWC;
+                uint32_t *wp = reinterpret_cast<uint32_t *>(win_s + r * RB + 4 * wc);
+                const uint32_t m4 = *wp;
+                if (!m4) continue;
+                uint32_t w4 = 0;
+                for (int b = 0; b < 4; ++b) {
+                    const uint32_t m = (m4 >> (8 * b)) & 255u;
+                    if (!m) continue;
+                    const uint32_t k = (uint32_t)__popc(m);
+                    uint32_t j;
+                    if (k == 1) {
+                        j = (uint32_t)(__ffs(m) - 1);
+                    } else {
+                        const int xc = x0 - 16 + 4 * wc + b, yc = y0 - 1 + r;
+                        j = pick_claimant(m, k, (uint64_t)yc * (uint64_t)W + (uint64_t)xc, t, d.seed);
+                    }
+                    w4 |= ((j + 1u) | (k >= 2 ? 0x10u : 0u)) << (8 * b);
+                }
+                *wp = w4;
+            }
+            __syncthreads();
+
+            // Owner pass, 16 cells per thread: evaporate (Eq. 3); an empty cell
+            // takes its winner's group and the deposit (Eq. 4/5); an agent whose
+            // target chose it leaves.
+            const int r = threadIdx.x >> 3, seg = threadIdx.x & 7;
+            const int y = y0 + r, x = x0 + 16 * seg;
+            const int li0 = r * TW + 16 * seg;
+            const int co = (r + 1) * RB + 16 + 16 * seg;  // this segment in occ_s / win_s
+            const int cp = (r + 2) * RB + 16 + 16 * seg;  // this segment in prop_s
+            if (aco) {
+                const float q = d.q;
+#pragma unroll
+                for (int g = 0; g < 2; ++g)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        float4 *v4 = reinterpret_cast<float4 *>(tau_s[g] + li0) + k;
+                        const float4 v = *v4;
+                        *v4 = make_float4(__fmul_rn(v.x, q), __fmul_rn(v.y, q), __fmul_rn(v.z, q),
+                                          __fmul_rn(v.w, q));
+                    }
+            }
+            const uint4 o = *reinterpret_cast<const uint4 *>(occ_s + co);
+            const uint4 w = *reinterpret_cast<const uint4 *>(win_s + co);
+            const uint4 pr = *reinterpret_cast<const uint4 *>(prop_s + cp);
+            uint4 no = o;
+            // only claimed cells (empty) and proposing agents can change
+            if (y < H && x < W && (w.x | w.y | w.z | w.w | pr.x | pr.y | pr.z | pr.w)) {
+                const uint32_t ow[4] = {o.x, o.y, o.z, o.w};
+                const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+                const uint32_t pw[4] = {pr.x, pr.y, pr.z, pr.w};
+                uint32_t nw[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+                for (int b = 0; b < 16; ++b) {
+                    const int og = (ow[b >> 2] >> (8 * (b & 3))) & 255u;
+                    if (og == 0) {
+                        const int wb = (ww[b >> 2] >> (8 * (b & 3))) & 255u;
+                        if (!wb) continue;
+                        const int j = (wb & 15) - 1;
+                        const int dx = kCodeDX[j + 1], dy = kCodeDY[j + 1];
+                        const int inc = occ_s[co + b + dy * RB + dx];
+                        nw[b >> 2] |= (uint32_t)inc << (8 * (b & 3));
+                        const uint64_t cell = (uint64_t)y * (uint64_t)W + (uint64_t)(x + b);
+                        const uint64_t rv = apply_move(d, cell, cell + (int64_t)dy * W + dx, inc, x + b,
+                                                       dx != 0 && dy != 0, t);
+                        ++cnt.moved;
+                        if (wb & 0x10) ++cnt.conflicts;
+                        const unsigned crossed = (unsigned)(rv >> 32);
+                        if (inc == 1) cnt.crossed_a += crossed; else cnt.crossed_b += crossed;
+                        if (aco) {
+                            float *v = &tau_s[inc == 1 ? 0 : 1][li0 + b];
+                            *v = __fadd_rn(*v, __uint_as_float((uint32_t)rv));
+                        }
+                    } else {
+                        const int code = (pw[b >> 2] >> (8 * (b & 3))) & 255u;
+                        if (!code) continue;
+                        const int wt = win_s[co + b + kCodeDY[code] * RB + kCodeDX[code]];
+                        if ((wt & 15) == 9 - code)  // this agent won its target: it leaves
+                            nw[b >> 2] &= ~(255u << (8 * (b & 3)));
+                    }
+                }
+                no = make_uint4(nw[0], nw[1], nw[2], nw[3]);
+            }
+            *reinterpret_cast<uint4 *>(occn_s + li0) = no;
+
+            // Results leave by TMA stores (cells outside the grid are skipped).
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                tma_store_2d(&gd->map_occ_out[p ^ 1], x0, y0, occn_s);
+                if (aco) {
+                    tma_store_2d(&gd->map_tau[0][p ^ 1], x0, y0, tau_s[0]);
+                    tma_store_2d(&gd->map_tau[1][p ^ 1], x0, y0, tau_s[1]);
+                }
+                bulk_commit();
+                bulk_wait_read();
+            }
+        }
+    }
+    flush_counts(d, cnt, item - __ldg(tile_prefix + s));
 }
 
 // ---------------------------------------------------------------------------
@@ -462,7 +1090,7 @@ __global__ void __launch_bounds__(kThreads)
 propose_plane_kernel(const ScenarioDesc *__restrict__ dp, uint8_t *__restrict__ prop, int t_off)
 {
     const ScenarioDesc &d = *dp;
-    const uint64_t t = *d.step + (uint64_t)t_off;
+    const uint64_t t = d.step + (uint64_t)t_off;
     if (t >= d.end_step) return;
     const int W = d.W, H = d.H;
     const int p = (int)(t & 1);
@@ -475,11 +1103,11 @@ propose_plane_kernel(const ScenarioDesc *__restrict__ dp, uint8_t *__restrict__ 
         int code = 0;
         if (g) {
             const int x = (int)(c % (size_t)W), y = (int)(c / (size_t)W);
-            const float *tp = d.tau[g - 1 < 2 ? g - 1 : 0][p];
+            const float *tp = d.tau[g == 2 ? 1 : 0][p];
             code = propose(
                 x, y, g, W, H, (uint64_t)c, t, d.seed, rp,
                 [&](int dx, int dy) { return (int)occ[(int64_t)c + (int64_t)dy * W + dx]; },
-                [&](int dx, int dy) { return tp[(int64_t)c + (int64_t)dy * W + dx]; });
+                tp ? tp + c : nullptr, W);
         }
         prop[c] = (uint8_t)code;
     }
@@ -490,7 +1118,7 @@ resolve_plane_kernel(const ScenarioDesc *__restrict__ dp, const uint8_t *__restr
                      int t_off)
 {
     const ScenarioDesc &d = *dp;
-    const uint64_t t = *d.step + (uint64_t)t_off;
+    const uint64_t t = d.step + (uint64_t)t_off;
     if (t >= d.end_step) return;
     const int W = d.W, H = d.H;
     const int p = (int)(t & 1);
@@ -523,22 +1151,45 @@ resolve_plane_kernel(const ScenarioDesc *__restrict__ dp, const uint8_t *__restr
                 d.tau[1][p ^ 1][c] = b;
             }
         }
-        flush_counts(d, cnt);
+        flush_counts(d, cnt, blockIdx.x);  // one counter slot per CTA
+    }
+}
+
+__global__ void advance_kernel(const ScenarioDesc *__restrict__ descs, int n, int k)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    ScenarioDesc *md = const_cast<ScenarioDesc *>(descs);
+    unsigned long long v = md[i].step + (unsigned long long)k;
+    if (v > md[i].end_step) v = md[i].end_step;
+    md[i].step = v;
+}
+
+// Totals of one scenario's counter slots (integer sums: order-free).
+__global__ void __launch_bounds__(256) sum_slots_kernel(const ScenarioDesc *__restrict__ dp,
+                                                        unsigned long long *__restrict__ out)
+{
+    const ScenarioDesc &d = *dp;
+    __shared__ unsigned long long red[kNumCounters][8];
+    unsigned long long acc[kNumCounters] = {0, 0, 0, 0};
+    for (uint32_t i = threadIdx.x; i < d.n_slots; i += blockDim.x)
+        for (int k = 0; k < kNumCounters; ++k) acc[k] += d.part[(size_t)i * kNumCounters + k];
+    for (int k = 0; k < kNumCounters; ++k) {
+        unsigned long long v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumCounters) {
+        unsigned long long v = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+        out[threadIdx.x] = v;
     }
 }
 
 // ---------------------------------------------------------------------------
 // Small helpers
 // ---------------------------------------------------------------------------
-__global__ void advance_kernel(const ScenarioDesc *__restrict__ descs, int n, int k)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    unsigned long long s = *descs[i].step + (unsigned long long)k;
-    if (s > descs[i].end_step) s = descs[i].end_step;
-    *descs[i].step = s;
-}
-
 __global__ void grid_counts_kernel(const ScenarioDesc *__restrict__ dp, int parity,
                                    unsigned int *__restrict__ out)
 {
@@ -569,17 +1220,6 @@ __global__ void grid_counts_kernel(const ScenarioDesc *__restrict__ dp, int pari
         if (pa) atomicAdd(&out[2], pa);
         if (pb) atomicAdd(&out[3], pb);
     }
-}
-
-__global__ void mask_ids_kernel(const ScenarioDesc *__restrict__ dp, int parity,
-                                uint32_t *__restrict__ out)
-{
-    const ScenarioDesc &d = *dp;
-    const size_t cells = (size_t)d.W * d.H;
-    const uint8_t *occ = d.occ[parity];
-    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells;
-         c += (size_t)gridDim.x * blockDim.x)
-        out[c] = occ[c] ? d.ids[c] : 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -624,12 +1264,13 @@ static cudaError_t ensure_fused_attr()
 
 template <int TW, int TH>
 static cudaError_t launch_fused_t(const ScenarioDesc *d_descs, const uint32_t *d_prefix, int n,
-                                  uint32_t total, int t_off, int grid, cudaStream_t stream)
+                                  uint32_t total, int t_off, unsigned int *done, int grid,
+                                  cudaStream_t stream)
 {
     cudaError_t e = ensure_fused_attr<TW, TH>();
     if (e != cudaSuccess) return e;
-    fused_step_kernel<TW, TH><<<grid, kThreads, FusedLayout<TW, TH>::SMEM, stream>>>(
-        d_descs, d_prefix, n, total, t_off);
+    fused_step_kernel<TW, TH><<<grid, kFusedThreads, FusedLayout<TW, TH>::SMEM, stream>>>(
+        d_descs, d_prefix, n, total, t_off, done);
     return cudaGetLastError();
 }
 
@@ -638,7 +1279,7 @@ static int blocks_per_sm_t()
 {
     if (ensure_fused_attr<TW, TH>() != cudaSuccess) return 1;
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fused_step_kernel<TW, TH>, kThreads,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fused_step_kernel<TW, TH>, kFusedThreads,
                                                       FusedLayout<TW, TH>::SMEM) != cudaSuccess)
         return 1;
     return b > 0 ? b : 1;
@@ -656,11 +1297,12 @@ bool tile_supported(int tile_w, int tile_h)
 
 cudaError_t launch_fused_step(const ScenarioDesc *d_descs, const uint32_t *d_tile_prefix, int n,
                               uint32_t total_tiles, int t_off, int tile_w, int tile_h, int grid,
-                              cudaStream_t stream)
+                              unsigned int *done, cudaStream_t stream)
 {
 #define PEDSIM_TILE_LAUNCH(w, h)                                                               \
     if (tile_w == w && tile_h == h)                                                            \
-        return launch_fused_t<w, h>(d_descs, d_tile_prefix, n, total_tiles, t_off, grid, stream);
+        return launch_fused_t<w, h>(d_descs, d_tile_prefix, n, total_tiles, t_off, done, grid,  \
+                                    stream);
     PEDSIM_TILES(PEDSIM_TILE_LAUNCH)
 #undef PEDSIM_TILE_LAUNCH
     return cudaErrorInvalidValue;
@@ -674,13 +1316,38 @@ int fused_blocks_per_sm(int tile_w, int tile_h)
     return 1;
 }
 
-int fused_threads() { return kThreads; }
+int fused_threads() { return kFusedThreads; }
+
+bool pipeline_tile_supported(int tile_w, int tile_h)
+{
+    return tile_w == kPipeTileW && (tile_h == 8 || tile_h == 16);
+}
+
+cudaError_t launch_pipeline_step(const ScenarioDesc *d_descs, const uint32_t *d_tile_prefix, int n,
+                                 uint32_t total_tiles, int t_off, int tile_h, cudaStream_t stream)
+{
+#define PEDSIM_PIPE(TH)                                                                        \
+    if (tile_h == TH) {                                                                        \
+        propose_tile_kernel<TH><<<total_tiles, 8 * TH, 0, stream>>>(d_descs, d_tile_prefix, n,  \
+                                                                    t_off);                    \
+        cudaError_t e = cudaGetLastError();                                                    \
+        if (e != cudaSuccess) return e;                                                        \
+        resolve_tile_kernel<TH><<<total_tiles, 8 * TH, 0, stream>>>(d_descs, d_tile_prefix, n, \
+                                                                    t_off);                    \
+        return cudaGetLastError();                                                             \
+    }
+    PEDSIM_PIPE(8)
+    PEDSIM_PIPE(16)
+#undef PEDSIM_PIPE
+    return cudaErrorInvalidValue;
+}
+
+int two_pass_grid(int W, int H) { return grid_for((size_t)W * H, kThreads, 152 * 16); }
 
 cudaError_t launch_two_pass_step(const ScenarioDesc *d_desc, uint8_t *d_prop, int W, int H,
                                  int t_off, cudaStream_t stream)
 {
-    const size_t cells = (size_t)W * H;
-    const int grid = grid_for(cells, kThreads, 152 * 16);
+    const int grid = two_pass_grid(W, H);
     propose_plane_kernel<<<grid, kThreads, 0, stream>>>(d_desc, d_prop, t_off);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -690,8 +1357,15 @@ cudaError_t launch_two_pass_step(const ScenarioDesc *d_desc, uint8_t *d_prop, in
 
 cudaError_t launch_advance(const ScenarioDesc *d_descs, int n, int k, cudaStream_t stream)
 {
-    if (n <= 0) return cudaSuccess;
+    if (n <= 0 || k == 0) return cudaSuccess;
     advance_kernel<<<(n + 255) / 256, 256, 0, stream>>>(d_descs, n, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_slots(const ScenarioDesc *d_desc, unsigned long long *d_out,
+                             cudaStream_t stream)
+{
+    sum_slots_kernel<<<1, 256, 0, stream>>>(d_desc, d_out);
     return cudaGetLastError();
 }
 
@@ -702,14 +1376,6 @@ cudaError_t launch_grid_counts(const ScenarioDesc *d_desc, int parity, int cells
     if (e != cudaSuccess) return e;
     grid_counts_kernel<<<grid_for((size_t)cells, kThreads, 1024), kThreads, 0, stream>>>(d_desc, parity,
                                                                                     d_out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_mask_ids(const ScenarioDesc *d_desc, int parity, int cells, uint32_t *d_out,
-                            cudaStream_t stream)
-{
-    mask_ids_kernel<<<grid_for((size_t)cells, kThreads, 2048), kThreads, 0, stream>>>(d_desc, parity,
-                                                                                 d_out);
     return cudaGetLastError();
 }
 

@@ -106,31 +106,16 @@ __device__ __forceinline__ float int_pow(float v, uint32_t e)
     return p;
 }
 
-// Proposal of an agent of group g (1 or 2) at (x, y) in a W x H grid at
-// step t.  `occ(dx, dy)` returns the occupancy byte of the in-grid cell at
-// that offset; `tau(dx, dy)` the agent's own-group pheromone there (ACO).
-// Returns the absolute direction code 0..8.
-template <class OccFn, class TauFn>
-__device__ __forceinline__ int propose(int x, int y, int g, int W, int H, uint64_t cell,
-                                       uint64_t step, uint64_t seed, const RuleParams &rp,
-                                       OccFn occ, TauFn tau)
+// Choice of an agent whose forward cell is blocked (Sec. II.A, II.B, IV.c).
+// avail: bit i set when frame neighbour i is in the grid and empty.  For ACO
+// the own-group pheromone at offset (dx, dy) from the agent is
+// tau_c[dy * tau_stride + dx] (tau_c points at the agent's own cell of a
+// plane or of a shared-memory tile).  Kept out of line: it is the rare,
+// heavy path (one Philox block).
+__device__ __noinline__ int choose_blocked(unsigned avail, int side, const float *tau_c,
+                                           int tau_stride, uint64_t cell, uint64_t step,
+                                           uint64_t seed, RuleParams rp)
 {
-    const int side = g - 1;
-    // an agent on its goal edge column stays (Sec. III)
-    if ((g == 1 && x == W - 1) || (g == 2 && x == 0)) return 0;
-
-    unsigned avail = 0;  // bit i set: frame neighbour i is in the grid and empty
-#pragma unroll
-    for (int i = 1; i <= 8; ++i) {
-        const int code = kFrameCode[side][i];
-        const int dx = kCodeDX[code], dy = kCodeDY[code];
-        const int nx = x + dx, ny = y + dy;
-        const bool inside = (unsigned)nx < (unsigned)W && (unsigned)ny < (unsigned)H;
-        if (inside && occ(dx, dy) == 0) avail |= 1u << i;
-    }
-    // forward first (Sec. III): no further calculation when #1 is free
-    if (avail & 2u) return kFrameCode[side][1];
-
     const Rand4 r = draw(seed, cell, step, kStreamPropose);
 
     if (rp.model == 1) {
@@ -141,7 +126,7 @@ __device__ __forceinline__ int propose(int x, int y, int g, int W, int H, uint64
             w[i] = 0.0f;
             if (avail & (1u << i)) {
                 const int code = kFrameCode[side][i];
-                const float tv = tau(kCodeDX[code], kCodeDY[code]);
+                const float tv = tau_c[kCodeDY[code] * tau_stride + kCodeDX[code]];
                 w[i] = __fmul_rn(int_pow(tv, rp.alpha), int_pow(kEta[i], rp.beta));
             }
             S = __fadd_rn(S, w[i]);
@@ -186,6 +171,46 @@ __device__ __forceinline__ int propose(int x, int y, int g, int W, int H, uint64
     return kFrameCode[side][pick];
 }
 
+// Proposal of an agent of group g (1 or 2) at (x, y) in a W x H grid at
+// step t.  `occ(dx, dy)` returns the occupancy byte of the in-grid cell at
+// that offset; tau_c / tau_stride locate the agent's own-group pheromone at
+// t (ACO, see choose_blocked).  Returns the absolute direction code 0..8.
+template <class OccFn>
+__device__ __forceinline__ int propose(int x, int y, int g, int W, int H, uint64_t cell,
+                                       uint64_t step, uint64_t seed, const RuleParams &rp,
+                                       OccFn occ, const float *tau_c, int tau_stride)
+{
+    const int side = g - 1;
+    // an agent on its goal edge column stays (Sec. III)
+    if ((g == 1 && x == W - 1) || (g == 2 && x == 0)) return 0;
+
+    unsigned avail = 0;  // bit i set: frame neighbour i is in the grid and empty
+#pragma unroll
+    for (int i = 1; i <= 8; ++i) {
+        const int code = kFrameCode[side][i];
+        const int dx = kCodeDX[code], dy = kCodeDY[code];
+        const int nx = x + dx, ny = y + dy;
+        const bool inside = (unsigned)nx < (unsigned)W && (unsigned)ny < (unsigned)H;
+        if (inside && occ(dx, dy) == 0) avail |= 1u << i;
+    }
+    // forward first (Sec. III): no further calculation when #1 is free
+    if (avail & 2u) return kFrameCode[side][1];
+    return choose_blocked(avail, side, tau_c, tau_stride, cell, step, seed, rp);
+}
+
+// Scan index of the winning claimant of a cell with claim mask m (bit j set:
+// the neighbour at scan offset j chose the cell) and k = popcount(m) >= 2:
+// claimant floor(r * k / 2^32) in scan order, r from Philox stream 2 keyed by
+// the target cell (Sec. IV.d).
+__device__ __noinline__ uint32_t pick_claimant(uint32_t m, uint32_t k, uint64_t cell,
+                                               uint64_t step, uint64_t seed)
+{
+    const Rand4 r = draw(seed, cell, step, kStreamConflict);
+    const uint32_t idx = (uint32_t)(((uint64_t)(uint32_t)(r.r0 >> 32) * (uint64_t)k) >> 32);
+    for (uint32_t u = 0; u < idx; ++u) m &= m - 1u;  // drop the idx lowest claimants
+    return (uint32_t)(__ffs(m) - 1);
+}
+
 // Gather resolution of target cell (x, y) at step t (Sec. IV.d): the
 // neighbours whose code points at it are the claimants, in scan order; one
 // wins uniformly (Philox stream 2 keyed by the target cell) when k >= 2.
@@ -196,25 +221,19 @@ __device__ __forceinline__ int resolve_winner(int x, int y, int W, int H, uint64
                                               uint64_t step, uint64_t seed, PropFn prop,
                                               int *k_out)
 {
-    int claim[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int k = 0;
+    uint32_t m = 0;  // bit j: the neighbour at scan offset j claims (x, y)
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int dx = kCodeDX[j + 1], dy = kCodeDY[j + 1];
         const int nx = x + dx, ny = y + dy;
         const bool inside = (unsigned)nx < (unsigned)W && (unsigned)ny < (unsigned)H;
-        if (inside && prop(dx, dy) == 8 - j) claim[k++] = j;
+        if (inside && prop(dx, dy) == 8 - j) m |= 1u << j;
     }
+    const int k = __popc(m);
     *k_out = k;
     if (k == 0) return -1;
-    if (k == 1) return claim[0];
-    const Rand4 r = draw(seed, cell, step, kStreamConflict);
-    const uint32_t idx = (uint32_t)(((uint64_t)(uint32_t)(r.r0 >> 32) * (uint64_t)k) >> 32);
-    int w = claim[0];
-#pragma unroll
-    for (int j = 1; j < 8; ++j)
-        if ((uint32_t)j == idx) w = claim[j];
-    return w;
+    if (k == 1) return __ffs(m) - 1;
+    return (int)pick_claimant(m, (uint32_t)k, cell, step, seed);
 }
 
 }  // namespace pedsim

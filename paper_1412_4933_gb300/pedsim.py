@@ -25,7 +25,7 @@ _lib = C.CDLL(LIB_PATH)
 
 OK, EINVAL, ENOMEM, ENOSPC, ECUDA, ETIMEDOUT, ENOENT = 0, -22, -12, -28, -5, -110, -2
 LEM, ACO = 0, 1
-VARIANT_FUSED, VARIANT_TWO_PASS = 0, 1
+VARIANT_TILED, VARIANT_TWO_PASS, VARIANT_FUSED = 0, 1, 2
 
 
 class SimParams(C.Structure):
@@ -70,6 +70,7 @@ _SIGS = {
     "sim_batch_step": (C.c_int, [_P, C.c_int]),
     "sim_batch_stats": (C.c_int, [_P, C.c_int, C.POINTER(SimStats)]),
     "sim_batch_read_grid": (C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
+    "sim_batch_set_variant": (C.c_int, [_P, C.c_int]),
     "sim_batch_set_tiling": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
     "sim_batch_device_status": (C.c_int, [_P]),
     "sim_batch_destroy": (None, [_P]),
@@ -260,6 +261,9 @@ class Batch:
 
     def step(self, n: int = 1) -> None:
         self._check(_lib.sim_batch_step(self._h, n))
+
+    def set_variant(self, variant: int) -> None:
+        self._check(_lib.sim_batch_set_variant(self._h, variant))
 
     def set_tiling(self, tile_w: int, tile_h: int, ctas_per_sm: int = 0) -> None:
         self._check(_lib.sim_batch_set_tiling(self._h, tile_w, tile_h, ctas_per_sm))

@@ -37,11 +37,11 @@ def assert_same(sim, orc, label, aco=True, agents=True):
         assert np.array_equal(a["tour"].view(np.uint32), o["tour"].view(np.uint32)), f"{label}: tour"
 
 
-def make_pair(sc, variant=P.VARIANT_FUSED, tiling=None):
+def make_pair(sc, variant=P.VARIANT_TILED, tiling=None):
     sim = P.Sim(sc.W, sc.H, P.params_of(sc))
+    sim.set_variant(variant)
     if tiling:
         sim.set_tiling(*tiling)
-    sim.set_variant(variant)
     sim.place(sc.seed)
     return sim, O.Oracle(sc.W, sc.H, oparams(sc), sc.seed)
 
@@ -62,7 +62,8 @@ def test_placement_matches_oracle(sc):
     assert sim.stats() == orc.stats()
 
 
-@pytest.mark.parametrize("variant", [P.VARIANT_FUSED, P.VARIANT_TWO_PASS], ids=["fused", "two_pass"])
+@pytest.mark.parametrize("variant", [P.VARIANT_TILED, P.VARIANT_TWO_PASS, P.VARIANT_FUSED],
+                         ids=["tiled", "two_pass", "fused"])
 @pytest.mark.parametrize("sc", SMALL, ids=lambda s: s.name)
 def test_every_step_small(sc, variant):
     sim, orc = make_pair(sc, variant)
@@ -76,11 +77,16 @@ def test_every_step_small(sc, variant):
     assert sim.device_status() == 0
 
 
-@pytest.mark.parametrize("tiling", [(32, 16), (64, 8), (64, 16), (128, 8), (128, 16)],
-                         ids=lambda t: f"{t[0]}x{t[1]}")
+TILINGS = [(P.VARIANT_TILED, 128, 8), (P.VARIANT_TILED, 128, 16),
+           (P.VARIANT_FUSED, 32, 16), (P.VARIANT_FUSED, 64, 8), (P.VARIANT_FUSED, 64, 16),
+           (P.VARIANT_FUSED, 128, 8), (P.VARIANT_FUSED, 128, 16)]
+
+
+@pytest.mark.parametrize("tiling", TILINGS, ids=lambda t: f"v{t[0]}_{t[1]}x{t[2]}")
 def test_every_tile_shape(tiling):
     sc = SMALL[2]
-    sim, orc = make_pair(sc, tiling=(*tiling, 0))
+    variant, tw, th = tiling
+    sim, orc = make_pair(sc, variant=variant, tiling=(tw, th, 0))
     for t in range(40):
         sim.step(1)
         orc.step(1)
