@@ -249,6 +249,46 @@ int sim_pool_live(const pool_t *pl);
 void sim_pool_destroy(pool_t *pl);
 const char *sim_pool_last_error(const pool_t *pl);
 
+/* ------------------------------------------------------------------------ */
+/* Allocation-free step.  The paper has no counterpart: this entry point     */
+/* exists for callers that cannot let a library allocate device memory while */
+/* they run -- applications that reserve all device memory up front under a  */
+/* fixed budget, frameworks whose caching allocator must account for every   */
+/* byte, code that records work into CUDA graphs.  It performs no cudaMalloc, */
+/* cudaFree or other allocation.                                             */
+/* ------------------------------------------------------------------------ */
+/* Advances the scenario (W, H, *p, seed) by one step, from step index `step`
+ * to step + 1, on caller-owned device buffers, asynchronously on `stream`
+ * (a cudaStream_t; NULL = legacy default stream).  Same rules and bit-exact
+ * results as sim_step.
+ *   occ_in / occ_out   device uint8 W*H, the occupancy at `step` / step+1
+ *                      (distinct buffers)
+ *   ids                device uint32 W*H, updated in place (valid at occupied
+ *                      cells; stale values may remain at vacated cells)
+ *   tauA_in, tauB_in / tauA_out, tauB_out
+ *                      device float W*H pheromone at step / step+1 (ACO only;
+ *                      may be NULL for LEM)
+ *   arrival, tour      device per-agent arrays of 2N+1 entries, updated in
+ *                      place (tour only for ACO with deposit_mode 1)
+ *   counters           device uint64[4] to which the step ADDS moved,
+ *                      conflicts, crossed[A], crossed[B]; may be NULL
+ * Scratch: the one-byte proposal plane between the two passes lives in a
+ * device array of the library sized for at most 16,777,216 (2^24) cells,
+ * e.g. 4096 x 4096; larger grids give PEDSIM_EINVAL.  The array exists on
+ * every GPU that loads the library until the library is unloaded.  It is
+ * shared by all calls (every call rewrites the part it uses before reading
+ * it), so calls whose work overlaps on the GPU -- on different streams or
+ * from different threads -- race and must be serialised by the caller.  The
+ * first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  Returns PEDSIM_EINVAL for invalid parameters or sizes, NULL or
+ * aliased buffers, PEDSIM_ECUDA when a launch fails.                         */
+int sim_step_noalloc(int W, int H, const sim_params *p, uint64_t seed, uint64_t step,
+                     const uint8_t *occ_in, uint8_t *occ_out, uint32_t *ids,
+                     const float *tauA_in, const float *tauB_in, float *tauA_out,
+                     float *tauB_out, uint32_t *arrival, float *tour,
+                     unsigned long long *counters, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -112,9 +112,9 @@ __device__ __forceinline__ float int_pow(float v, uint32_t e)
 // tau_c[dy * tau_stride + dx] (tau_c points at the agent's own cell of a
 // plane or of a shared-memory tile).  Kept out of line: it is the rare,
 // heavy path (one Philox block).
-__device__ __noinline__ int choose_blocked(unsigned avail, int side, const float *tau_c,
-                                           int tau_stride, uint64_t cell, uint64_t step,
-                                           uint64_t seed, RuleParams rp)
+static __device__ __noinline__ int choose_blocked(unsigned avail, int side, const float *tau_c,
+                                                  int tau_stride, uint64_t cell, uint64_t step,
+                                                  uint64_t seed, RuleParams rp)
 {
     const Rand4 r = draw(seed, cell, step, kStreamPropose);
 
@@ -202,8 +202,8 @@ __device__ __forceinline__ int propose(int x, int y, int g, int W, int H, uint64
 // the neighbour at scan offset j chose the cell) and k = popcount(m) >= 2:
 // claimant floor(r * k / 2^32) in scan order, r from Philox stream 2 keyed by
 // the target cell (Sec. IV.d).
-__device__ __noinline__ uint32_t pick_claimant(uint32_t m, uint32_t k, uint64_t cell,
-                                               uint64_t step, uint64_t seed)
+static __device__ __noinline__ uint32_t pick_claimant(uint32_t m, uint32_t k, uint64_t cell,
+                                                      uint64_t step, uint64_t seed)
 {
     const Rand4 r = draw(seed, cell, step, kStreamConflict);
     const uint32_t idx = (uint32_t)(((uint64_t)(uint32_t)(r.r0 >> 32) * (uint64_t)k) >> 32);

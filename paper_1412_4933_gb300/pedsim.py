@@ -88,6 +88,8 @@ _SIGS = {
     "sim_pool_live": (C.c_int, [_P]),
     "sim_pool_destroy": (None, [_P]),
     "sim_pool_last_error": (C.c_char_p, [_P]),
+    "sim_step_noalloc": (C.c_int, [C.c_int, C.c_int, C.POINTER(SimParams), C.c_uint64, C.c_uint64,
+                                   _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -367,6 +369,26 @@ class Pool:
 
     def __del__(self):
         self.close()
+
+
+NOALLOC_MAX_CELLS = 1 << 24
+
+
+def step_noalloc(W, H, params: SimParams, seed: int, step: int, occ_in, occ_out, ids, tauA_in=None,
+                 tauB_in=None, tauA_out=None, tauB_out=None, arrival=None, tour=None,
+                 counters=None, stream=None) -> int:
+    """One allocation-free step on caller-owned device tensors (anything with
+    ``data_ptr()``); returns the C status code.  For callers that must not let
+    the library allocate device memory: the scratch it needs lives in a fixed
+    device array of the library (at most NOALLOC_MAX_CELLS cells)."""
+    ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+    if stream is None:
+        stream = _default_stream()
+    elif not isinstance(stream, C.c_void_p):
+        stream = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    return int(_lib.sim_step_noalloc(W, H, C.byref(params), seed, step, ptr(occ_in), ptr(occ_out),
+                                     ptr(ids), ptr(tauA_in), ptr(tauB_in), ptr(tauA_out),
+                                     ptr(tauB_out), ptr(arrival), ptr(tour), ptr(counters), stream))
 
 
 def exported_symbols():
