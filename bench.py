@@ -270,9 +270,14 @@ def e2e_run(P, torch, sc, stream, reps: int):
 
 
 def batched_leg(P, torch, stream, count=256, steps=500):
+    """The 256-scenario batch: autotuned launch configuration, then `steps`
+    steps in batched launches, vs one launch per scenario per step."""
+    from paper_1412_4933_gb300 import autotune
     scs = WL.batched_scenarios(count=count, steps=steps)
     cells = sum(s.cells for s in scs)
+    choice = autotune.tune(scs, steps=16, stream=stream)
     batch = P.Batch(scs, stream=stream)
+    autotune.apply(batch, choice)
     batch.step(16)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -281,8 +286,8 @@ def batched_leg(P, torch, stream, count=256, steps=500):
     t_batch = time.perf_counter() - t0
     status = batch.device_status()
     batch.close()
-    # one launch per scenario per step, same scenarios and steps (a sample of
-    # 32 scenarios, scaled by cells)
+    # one launch per scenario per step, same scenarios (a sample of 32,
+    # scaled by cells)
     sample = scs[:32]
     sims = []
     for s in sample:
@@ -302,6 +307,8 @@ def batched_leg(P, torch, stream, count=256, steps=500):
         sim.close()
     single_rate = sum(s.cells for s in sample) * (steps // 10) / t_single
     return {"scenarios": count, "steps": steps, "cells": cells,
+            "launch_config": {"variant": choice[0], "tile": [choice[1], choice[2]],
+                              "ctas_per_sm": choice[3]},
             "scenarios_per_s": count / t_batch,
             "cell_updates_per_s": cells * steps / t_batch,
             "one_launch_per_scenario_cell_updates_per_s": single_rate,
@@ -310,37 +317,16 @@ def batched_leg(P, torch, stream, count=256, steps=500):
 
 
 def serving_leg(P, torch, stream, n_requests=200, budget_frac=0.5, chunk=16):
+    """Poisson request stream (200/s) through the continuous-batching loop."""
+    from paper_1412_4933_gb300 import serving
     reqs = WL.serving_requests(n_requests)
     free, _ = torch.cuda.mem_get_info()
-    pool = P.Pool(int(free * budget_frac), 512, stream=stream)
-    pending = list(reqs)
-    live = {}
-    latencies = []
-    t_start = time.perf_counter()
-    done_cells = 0
-    while pending or live:
-        now = time.perf_counter() - t_start
-        while pending and pending[0].arrival_s <= now:
-            slot = pool.admit(pending[0].scenario)
-            if slot is None:
-                break
-            live[slot] = pending.pop(0)
-        if not live:
-            if pending:
-                time.sleep(max(0.0, pending[0].arrival_s - (time.perf_counter() - t_start)))
-            continue
-        pool.step(chunk)
-        for slot in pool.finished():
-            r = live.pop(slot)
-            latencies.append(time.perf_counter() - t_start - r.arrival_s)
-            done_cells += r.scenario.cells * r.scenario.steps
-            pool.release(slot)
-    total = time.perf_counter() - t_start
-    pool.close()
-    lat = np.array(latencies)
-    return {"requests": n_requests, "rate_per_s": 200.0, "p50_s": float(np.percentile(lat, 50)),
-            "p99_s": float(np.percentile(lat, 99)), "scenarios_per_s": n_requests / total,
-            "cell_updates_per_s": done_cells / total, "hbm_budget_frac": budget_frac}
+    loop = serving.ServingLoop(int(free * budget_frac), 512, chunk=chunk, stream=stream)
+    rep = loop.run(reqs)
+    loop.close()
+    out = rep.summary()
+    out.update({"rate_per_s": 200.0, "hbm_budget_frac": budget_frac, "chunk_steps": chunk})
+    return out
 
 
 def run_gpu(args, sc):

@@ -142,3 +142,11 @@ def random_occupancy(W: int, H: int, density: float, seed: int):
     n = int(filled.sum())
     ids[filled] = rng.permutation(n).astype(np.uint32) + 1
     return occ, ids
+
+
+def shard(items, rank: int, world: int):
+    """Independent scenarios split across ranks round-robin (no exchange is
+    needed: every scenario's result depends on its own seed only)."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("bad rank/world")
+    return list(items)[rank::world]
