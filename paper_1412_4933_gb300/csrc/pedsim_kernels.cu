@@ -82,6 +82,19 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// Programmatic dependent launch: wait until the preceding kernel in the
+// stream has completed and its memory is visible (no-op when the launch did
+// not overlap), and let the next kernel start its prologue.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+// Starts fetching a tensor map (kept in global memory) into the TMA unit's
+// descriptor cache, so that the copy issued later does not wait for it.
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
+}
+
 // Shared -> global tiled bulk copy (elements outside the tensor are skipped).
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, const void *src)
 {
@@ -764,6 +777,23 @@ fused_step_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__rest
 constexpr int kPipeTileW = 128;
 constexpr int kPipeRowB = kPipeTileW + 32;  // staged row: 16-column halo either side
 
+// Bit 8*b + 7 set for every nonzero byte b of v (bytes tested without carries
+// between them).
+__device__ __forceinline__ uint32_t nonzero_bytes(uint32_t v)
+{
+    return (((v & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | v) & 0x80808080u;
+}
+
+// One thread waits (bounded) for the TMA copies behind `bar`; the rest of the
+// CTA blocks in the barrier instead of polling.  Returns false for every
+// thread when the wait gave up.
+__device__ __forceinline__ bool cta_wait_tma(uint64_t *bar, uint32_t parity)
+{
+    bool ok = true;
+    if (threadIdx.x == 0) ok = mbar_wait_bounded(bar, parity);
+    return __syncthreads_and(ok);
+}
+
 // Appends `n` entries of this thread to a shared list with one shared atomic
 // per warp; returns the first slot of this thread.  All 32 lanes must call.
 __device__ __forceinline__ int warp_reserve(unsigned int *counter, int n)
@@ -822,6 +852,15 @@ propose_tile_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__re
     const uint32_t item = blockIdx.x;
     const int s = scenario_of(tile_prefix, n_scen, item);
     const ScenarioDesc *gd = descs + s;
+    if (threadIdx.x == 32) {
+        prefetch_tensormap(&gd->map_occ[0]);
+        prefetch_tensormap(&gd->map_occ[1]);
+    }
+    // Everything below reads the previous kernel's results (the occupancy
+    // of the previous resolution, the step index of an advance): wait for it,
+    // then let the resolution kernel of this step start its prologue.
+    pdl_wait();
+    pdl_trigger();
     load_header(&hdr_s, gd);
     __syncthreads();
     const ScenarioDesc &d = hdr_s;
@@ -839,8 +878,7 @@ propose_tile_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__re
         tma_load_2d(occ_s, &gd->map_occ[p], x0 - 16, y0 - 1, &bar);
     }
     __syncthreads();
-    const bool ok = mbar_wait_bounded(&bar, 0);
-    if (!__syncthreads_and(ok)) {
+    if (!cta_wait_tma(&bar, 0)) {
         if (threadIdx.x == 0) atomicExch(d.error, kErrTimeout);
         return;
     }
@@ -894,15 +932,11 @@ propose_tile_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__re
                 tp ? tp + cell : nullptr, W);
         }
     }
-    // The tile of codes leaves by one TMA store (cells outside the grid are
-    // skipped by the copy).
-    fence_proxy_async_smem();
+    // Each thread stores its 16 codes (cells outside the grid are skipped).
     __syncthreads();
-    if (threadIdx.x == 0) {
-        tma_store_2d(&gd->map_prop_out, x0, y0, code_s);
-        bulk_commit();
-        bulk_wait_read();
-    }
+    if (y < H && x < W)
+        *reinterpret_cast<uint4 *>(d.prop + (uint64_t)y * (uint64_t)W + x) =
+            *reinterpret_cast<const uint4 *>(code_s + r * TW + 16 * seg);
 }
 
 template <int TH>
@@ -911,67 +945,106 @@ resolve_tile_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__re
                     int n_scen, int t_off)
 {
     constexpr int NT = 8 * TH, RB = kPipeRowB, TW = kPipeTileW;
-    constexpr int NWC = TW / 4 + 2;  // 32-bit word columns covering x0-4 .. x0+TW+3
     __shared__ __align__(128) float tau_s[2][TH * TW];
     __shared__ __align__(128) uint8_t prop_s[(TH + 4) * RB];  // rows y0-2 .. y0+TH+1
     __shared__ __align__(128) uint8_t occ_s[(TH + 2) * RB];   // rows y0-1 .. y0+TH
     __shared__ __align__(128) uint8_t win_s[(TH + 2) * RB];   // claim masks, then winners
-    __shared__ __align__(128) uint8_t occn_s[TH * TW];
+    __shared__ uint16_t moves[TH * TW];                        // tile cells receiving an agent
+    __shared__ unsigned int n_moves;
     __shared__ __align__(128) ScenarioDesc hdr_s;  // header part only
     __shared__ __align__(8) uint64_t bar;
     const uint32_t item = blockIdx.x;
     const int s = scenario_of(tile_prefix, n_scen, item);
     const ScenarioDesc *gd = descs + s;
+    if (threadIdx.x == 32) {  // maps are fetched while the header is read
+        prefetch_tensormap(&gd->map_prop);
+        prefetch_tensormap(&gd->map_occ[0]);
+        prefetch_tensormap(&gd->map_occ[1]);
+        prefetch_tensormap(&gd->map_tau[0][0]);
+        prefetch_tensormap(&gd->map_tau[0][1]);
+        prefetch_tensormap(&gd->map_tau[1][0]);
+        prefetch_tensormap(&gd->map_tau[1][1]);
+    }
     load_header(&hdr_s, gd);
-    // claim masks start at zero
+    // claim masks and the move list start empty
     for (int i = threadIdx.x; i < (TH + 2) * RB / 16; i += NT)
         reinterpret_cast<uint4 *>(win_s)[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (threadIdx.x == 0) n_moves = 0;
     __syncthreads();
     const ScenarioDesc &d = hdr_s;
     const uint64_t t = d.step + (uint64_t)t_off;
     Counts cnt;
-    if (t < d.end_step) {
+    if (t >= d.end_step) {
+        pdl_wait();
+        pdl_trigger();
+    } else {
         const uint32_t local = item - __ldg(tile_prefix + s);
         const int ty = (int)(local / (uint32_t)d.tiles_x), tx = (int)(local % (uint32_t)d.tiles_x);
         const int x0 = tx * TW, y0 = ty * TH;
         const int p = (int)(t & 1);
         const bool aco = d.model == 1;
         if (threadIdx.x == 0) {
+            // The occupancy and pheromone at t come from the resolution of the
+            // step before, complete before this step's proposal kernel
+            // started: they are copied while the proposal kernel still runs.
             mbar_init(&bar, 1);
             fence_mbarrier_init();
             mbar_arrive_expect_tx(&bar, (TH + 4) * RB + (TH + 2) * RB + (aco ? 2 * TH * TW * 4 : 0));
-            tma_load_2d(prop_s, &gd->map_prop, x0 - 16, y0 - 2, &bar);
             tma_load_2d(occ_s, &gd->map_occ[p], x0 - 16, y0 - 1, &bar);
             if (aco) {
                 tma_load_2d(tau_s[0], &gd->map_tau[0][p], x0, y0, &bar);
                 tma_load_2d(tau_s[1], &gd->map_tau[1][p], x0, y0, &bar);
             }
+            // the proposals are the proposal kernel's output
+            pdl_wait();
+            tma_load_2d(prop_s, &gd->map_prop, x0 - 16, y0 - 2, &bar);
         }
+        pdl_wait();
+        pdl_trigger();
         const int W = d.W, H = d.H;
         __syncthreads();  // barrier initialised
-        const bool ok = mbar_wait_bounded(&bar, 0);
-        if (!__syncthreads_and(ok)) {
+        if (!cta_wait_tma(&bar, 0)) {
             if (threadIdx.x == 0) atomicExch(d.error, kErrTimeout);
         } else {
             // Claim pass: every proposal of the tile and its 2-ring that targets
             // the tile or its 1-ring sets bit (8 - code) of the target's mask
             // (the claimant's scan offset seen from the target).  Cells outside
-            // the grid hold no proposal (TMA zero fill).
-            for (int i = threadIdx.x; i < (TH + 4) * NWC; i += NT) {
-                const int r = i / NWC, wc = 3 + i % NWC;
-                const uint32_t p4 = *reinterpret_cast<const uint32_t *>(prop_s + r * RB + 4 * wc);
-                if (!p4) continue;
+            // the grid hold no proposal (TMA zero fill).  16 bytes per load;
+            // only nonzero bytes are visited.
+            constexpr int NQ = RB / 16;  // 16-byte columns per staged row
+            // Evaporation of both pheromone tiles (Eq. 3), contiguous float4 per
+            // thread (conflict-free); deposits are added after the barrier.
+            if (aco) {
+                const float q = d.q;
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int code = (p4 >> (8 * b)) & 255u;
-                    const int cx = 4 * wc + b;
-                    if (!code || cx < 14 || cx > TW + 17) continue;
-                    const int tr = r - 1 + kCodeDY[code];  // target row in win_s
-                    const int tc = cx + kCodeDX[code];
-                    if (tr >= 0 && tr < TH + 2 && tc >= 15 && tc <= TW + 16) {
-                        const int idx = tr * RB + tc;
-                        atomicOr(reinterpret_cast<unsigned int *>(win_s + (idx & ~3)),
-                                 (1u << (8 - code)) << (8 * (idx & 3)));
+                for (int g = 0; g < 2; ++g)
+                    for (int i = threadIdx.x; i < TH * TW / 4; i += NT) {
+                        float4 *v4 = reinterpret_cast<float4 *>(tau_s[g]) + i;
+                        const float4 v = *v4;
+                        *v4 = make_float4(__fmul_rn(v.x, q), __fmul_rn(v.y, q), __fmul_rn(v.z, q),
+                                          __fmul_rn(v.w, q));
+                    }
+            }
+            for (int i = threadIdx.x; i < (TH + 4) * NQ; i += NT) {
+                const int r = i / NQ, q0 = 16 * (i % NQ);
+                const uint4 v = *reinterpret_cast<const uint4 *>(prop_s + r * RB + q0);
+                const uint32_t vw[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    uint32_t nz = nonzero_bytes(vw[w]);
+                    while (nz) {
+                        const int b = (__ffs(nz) - 1) >> 3;
+                        nz &= nz - 1;
+                        const int cx = q0 + 4 * w + b;
+                        if (cx < 14 || cx > TW + 17) continue;
+                        const int code = (vw[w] >> (8 * b)) & 255u;
+                        const int tr = r - 1 + kCodeDY[code];  // target row in win_s
+                        const int tc = cx + kCodeDX[code];
+                        if (tr >= 0 && tr < TH + 2 && tc >= 15 && tc <= TW + 16) {
+                            const int idx = tr * RB + tc;
+                            atomicOr(reinterpret_cast<unsigned int *>(win_s + (idx & ~3)),
+                                     (1u << (8 - code)) << (8 * (idx & 3)));
+                        }
                     }
                 }
             }
@@ -980,103 +1053,126 @@ resolve_tile_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__re
             // Winner pass (Sec. IV.d): the only claimant, or claimant
             // floor(r * k / 2^32) in scan order from Philox stream 2 at the
             // target cell; the byte becomes (scan index + 1) | 0x10 if k >= 2.
-            for (int i = threadIdx.x; i < (TH + 2) * NWC; i += NT) {
-                const int r = i / NWC, wc = 3 + i % NWC;
-                uint32_t *wp = reinterpret_cast<uint32_t *>(win_s + r * RB + 4 * wc);
-                const uint32_t m4 = *wp;
-                if (!m4) continue;
-                uint32_t w4 = 0;
-                for (int b = 0; b < 4; ++b) {
-                    const uint32_t m = (m4 >> (8 * b)) & 255u;
-                    if (!m) continue;
-                    const uint32_t k = (uint32_t)__popc(m);
-                    uint32_t j;
-                    if (k == 1) {
-                        j = (uint32_t)(__ffs(m) - 1);
-                    } else {
-                        const int xc = x0 - 16 + 4 * wc + b, yc = y0 - 1 + r;
-                        j = pick_claimant(m, k, (uint64_t)yc * (uint64_t)W + (uint64_t)xc, t, d.seed);
+            for (int i = threadIdx.x; i < (TH + 2) * NQ; i += NT) {
+                const int r = i / NQ, q0 = 16 * (i % NQ);
+                uint4 *wp = reinterpret_cast<uint4 *>(win_s + r * RB + q0);
+                const uint4 mv = *wp;
+                if (!(mv.x | mv.y | mv.z | mv.w)) continue;
+                uint32_t mw[4] = {mv.x, mv.y, mv.z, mv.w};
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    uint32_t nz = nonzero_bytes(mw[w]);
+                    uint32_t out = 0;
+                    while (nz) {
+                        const int b = (__ffs(nz) - 1) >> 3;
+                        nz &= nz - 1;
+                        const uint32_t m = (mw[w] >> (8 * b)) & 255u;
+                        const uint32_t k = (uint32_t)__popc(m);
+                        uint32_t j;
+                        if (k == 1) {
+                            j = (uint32_t)(__ffs(m) - 1);
+                        } else {
+                            const int xc = x0 - 16 + q0 + 4 * w + b, yc = y0 - 1 + r;
+                            j = pick_claimant(m, k, (uint64_t)yc * (uint64_t)W + (uint64_t)xc, t,
+                                              d.seed);
+                        }
+                        out |= ((j + 1u) | (k >= 2 ? 0x10u : 0u)) << (8 * b);
                     }
-                    w4 |= ((j + 1u) | (k >= 2 ? 0x10u : 0u)) << (8 * b);
+                    mw[w] = out;
                 }
-                *wp = w4;
+                *wp = make_uint4(mw[0], mw[1], mw[2], mw[3]);
             }
             __syncthreads();
 
-            // Owner pass, 16 cells per thread: evaporate (Eq. 3); an empty cell
-            // takes its winner's group and the deposit (Eq. 4/5); an agent whose
-            // target chose it leaves.
+            // Owner pass, 16 cells per thread: an empty cell takes its winner's
+            // group, an agent whose target chose it leaves.  Only cells with a
+            // winner byte (empty, claimed) or a proposal (agents) can change.
+            // Cells that receive an agent go to the move list.
             const int r = threadIdx.x >> 3, seg = threadIdx.x & 7;
             const int y = y0 + r, x = x0 + 16 * seg;
             const int li0 = r * TW + 16 * seg;
             const int co = (r + 1) * RB + 16 + 16 * seg;  // this segment in occ_s / win_s
             const int cp = (r + 2) * RB + 16 + 16 * seg;  // this segment in prop_s
-            if (aco) {
-                const float q = d.q;
-#pragma unroll
-                for (int g = 0; g < 2; ++g)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        float4 *v4 = reinterpret_cast<float4 *>(tau_s[g] + li0) + k;
-                        const float4 v = *v4;
-                        *v4 = make_float4(__fmul_rn(v.x, q), __fmul_rn(v.y, q), __fmul_rn(v.z, q),
-                                          __fmul_rn(v.w, q));
-                    }
-            }
             const uint4 o = *reinterpret_cast<const uint4 *>(occ_s + co);
             const uint4 w = *reinterpret_cast<const uint4 *>(win_s + co);
             const uint4 pr = *reinterpret_cast<const uint4 *>(prop_s + cp);
             uint4 no = o;
-            // only claimed cells (empty) and proposing agents can change
+            uint32_t arrivals = 0;  // bit b: cell b of the segment receives an agent
             if (y < H && x < W && (w.x | w.y | w.z | w.w | pr.x | pr.y | pr.z | pr.w)) {
-                const uint32_t ow[4] = {o.x, o.y, o.z, o.w};
                 const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
                 const uint32_t pw[4] = {pr.x, pr.y, pr.z, pr.w};
                 uint32_t nw[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
-                for (int b = 0; b < 16; ++b) {
-                    const int og = (ow[b >> 2] >> (8 * (b & 3))) & 255u;
-                    if (og == 0) {
-                        const int wb = (ww[b >> 2] >> (8 * (b & 3))) & 255u;
-                        if (!wb) continue;
-                        const int j = (wb & 15) - 1;
-                        const int dx = kCodeDX[j + 1], dy = kCodeDY[j + 1];
-                        const int inc = occ_s[co + b + dy * RB + dx];
-                        nw[b >> 2] |= (uint32_t)inc << (8 * (b & 3));
-                        const uint64_t cell = (uint64_t)y * (uint64_t)W + (uint64_t)(x + b);
-                        const uint64_t rv = apply_move(d, cell, cell + (int64_t)dy * W + dx, inc, x + b,
-                                                       dx != 0 && dy != 0, t);
-                        ++cnt.moved;
-                        if (wb & 0x10) ++cnt.conflicts;
-                        const unsigned crossed = (unsigned)(rv >> 32);
-                        if (inc == 1) cnt.crossed_a += crossed; else cnt.crossed_b += crossed;
-                        if (aco) {
-                            float *v = &tau_s[inc == 1 ? 0 : 1][li0 + b];
-                            *v = __fadd_rn(*v, __uint_as_float((uint32_t)rv));
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t nz = nonzero_bytes(ww[q] | pw[q]);
+                    while (nz) {
+                        const int bb = (__ffs(nz) - 1) >> 3;
+                        nz &= nz - 1;
+                        const int b = 4 * q + bb;
+                        const int wb = (ww[q] >> (8 * bb)) & 255u;
+                        if (wb) {  // empty cell with a winner
+                            const int j = (wb & 15) - 1;
+                            nw[q] |= (uint32_t)occ_s[co + b + kCodeDY[j + 1] * RB + kCodeDX[j + 1]]
+                                     << (8 * bb);
+                            arrivals |= 1u << b;
+                        } else {  // an agent with a proposal
+                            const int code = (pw[q] >> (8 * bb)) & 255u;
+                            const int wt = win_s[co + b + kCodeDY[code] * RB + kCodeDX[code]];
+                            if ((wt & 15) == 9 - code)  // this agent won its target: it leaves
+                                nw[q] &= ~(255u << (8 * bb));
                         }
-                    } else {
-                        const int code = (pw[b >> 2] >> (8 * (b & 3))) & 255u;
-                        if (!code) continue;
-                        const int wt = win_s[co + b + kCodeDY[code] * RB + kCodeDX[code]];
-                        if ((wt & 15) == 9 - code)  // this agent won its target: it leaves
-                            nw[b >> 2] &= ~(255u << (8 * (b & 3)));
                     }
                 }
                 no = make_uint4(nw[0], nw[1], nw[2], nw[3]);
             }
-            *reinterpret_cast<uint4 *>(occn_s + li0) = no;
-
-            // Results leave by TMA stores (cells outside the grid are skipped).
-            fence_proxy_async_smem();
+            if (y < H && x < W)
+                *reinterpret_cast<uint4 *>(d.occ[p ^ 1] + (uint64_t)y * (uint64_t)W + x) = no;
+            int slot = warp_reserve(&n_moves, __popc(arrivals));
+            while (arrivals) {
+                const int b = __ffs(arrivals) - 1;
+                arrivals &= arrivals - 1;
+                moves[slot++] = (uint16_t)(li0 + b);
+            }
             __syncthreads();
-            if (threadIdx.x == 0) {
-                tma_store_2d(&gd->map_occ_out[p ^ 1], x0, y0, occn_s);
+
+            // Move pass, one move per thread (their id / arrival / tour round
+            // trips overlap): the agent's id follows it, Eq. 5 extends its tour,
+            // its first entry into the opposite band is recorded (Sec. VI), and
+            // its deposit (Eq. 4/5) lands on the evaporated pheromone.
+            const int nm = (int)n_moves;
+            for (int i = threadIdx.x; i < nm; i += NT) {
+                const int li = moves[i];
+                const int ly = li / TW, lx = li - ly * TW;
+                const int wb = win_s[(ly + 1) * RB + 16 + lx];
+                const int j = (wb & 15) - 1;
+                const int dx = kCodeDX[j + 1], dy = kCodeDY[j + 1];
+                const int inc = occ_s[(ly + 1 + dy) * RB + 16 + lx + dx];
+                const uint64_t cell = (uint64_t)(y0 + ly) * (uint64_t)W + (uint64_t)(x0 + lx);
+                const uint64_t rv = apply_move(d, cell, cell + (int64_t)dy * W + dx, inc, x0 + lx,
+                                               dx != 0 && dy != 0, t);
+                ++cnt.moved;
+                if (wb & 0x10) ++cnt.conflicts;
+                const unsigned crossed = (unsigned)(rv >> 32);
+                if (inc == 1) cnt.crossed_a += crossed; else cnt.crossed_b += crossed;
                 if (aco) {
-                    tma_store_2d(&gd->map_tau[0][p ^ 1], x0, y0, tau_s[0]);
-                    tma_store_2d(&gd->map_tau[1][p ^ 1], x0, y0, tau_s[1]);
+                    float *v = &tau_s[inc == 1 ? 0 : 1][li];
+                    *v = __fadd_rn(*v, __uint_as_float((uint32_t)rv));
                 }
-                bulk_commit();
-                bulk_wait_read();
+            }
+            // Pheromone leaves by 16-byte stores (which, unlike a bulk copy's
+            // read of shared memory, do not hold the CTA back) once every
+            // deposit is in.
+            if (aco) {
+                __syncthreads();
+#pragma unroll
+                for (int g = 0; g < 2; ++g)
+                    for (int i = threadIdx.x; i < TH * TW / 4; i += NT) {
+                        const int ry = i / (TW / 4), cx4 = 4 * (i % (TW / 4));
+                        if (y0 + ry < H && x0 + cx4 < W)
+                            *reinterpret_cast<float4 *>(d.tau[g][p ^ 1] + (uint64_t)(y0 + ry) * W +
+                                                        x0 + cx4) =
+                                reinterpret_cast<const float4 *>(tau_s[g])[i];
+                    }
             }
         }
     }
@@ -1318,6 +1414,25 @@ int fused_blocks_per_sm(int tile_w, int tile_h)
 
 int fused_threads() { return kFusedThreads; }
 
+// Launch that may overlap the previous kernel in the stream (programmatic
+// dependent launch); the kernel orders itself with pdl_wait.
+template <class... KArgs, class... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block,
+                              cudaStream_t stream, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 bool pipeline_tile_supported(int tile_w, int tile_h)
 {
     return tile_w == kPipeTileW && (tile_h == 8 || tile_h == 16);
@@ -1328,13 +1443,11 @@ cudaError_t launch_pipeline_step(const ScenarioDesc *d_descs, const uint32_t *d_
 {
 #define PEDSIM_PIPE(TH)                                                                        \
     if (tile_h == TH) {                                                                        \
-        propose_tile_kernel<TH><<<total_tiles, 8 * TH, 0, stream>>>(d_descs, d_tile_prefix, n,  \
-                                                                    t_off);                    \
-        cudaError_t e = cudaGetLastError();                                                    \
+        cudaError_t e = launch_pdl(propose_tile_kernel<TH>, total_tiles, 8 * TH, stream, d_descs, \
+                                   d_tile_prefix, n, t_off);                                   \
         if (e != cudaSuccess) return e;                                                        \
-        resolve_tile_kernel<TH><<<total_tiles, 8 * TH, 0, stream>>>(d_descs, d_tile_prefix, n, \
-                                                                    t_off);                    \
-        return cudaGetLastError();                                                             \
+        return launch_pdl(resolve_tile_kernel<TH>, total_tiles, 8 * TH, stream, d_descs,       \
+                          d_tile_prefix, n, t_off);                                            \
     }
     PEDSIM_PIPE(8)
     PEDSIM_PIPE(16)
