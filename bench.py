@@ -48,7 +48,7 @@ L2_FLUSH_BYTES = 512 << 20
 ALGO_BYTES_PER_CELL = {WL.LEM: 2, WL.ACO: 18}
 KERNEL_SOURCES = ["paper_1412_4933_gb300/csrc/pedsim_kernels.cu",
                   "paper_1412_4933_gb300/csrc/pedsim_rules.cuh"]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_step_aco_2048_traffic.md")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "tiled_step_aco_2048x2048_traffic.md")
 
 
 def kernel_source_hash() -> str:
@@ -69,7 +69,7 @@ def measured_peak():
 
 
 def recorded_traffic():
-    """Per-launch DRAM bytes of the fused kernel from the committed ncu
+    """Per-step DRAM bytes of the two step kernels from the committed ncu
     summary, if it was taken on the current kernel source."""
     try:
         text = open(TRAFFIC_FILE).read()
@@ -269,6 +269,29 @@ def e2e_run(P, torch, sc, stream, reps: int):
             "seconds_per_run": best, "final_moved": st["moved"]}
 
 
+def probe_leg(P, torch, stream, steps=20):
+    """The 8192^2 probe at the same density (1.6M agents): 1.2 GB of planes
+    per step, far beyond the 129 MB L2, so every step streams from HBM."""
+    sc = WL.ACO_8192
+    sim = P.Sim(sc.W, sc.H, P.params_of(sc), stream=stream)
+    sim.place(sc.seed)
+    sim.step(16)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dt = e0.elapsed_time(e1) * 1e-3 / steps
+    status = sim.device_status()
+    sim.close()
+    algo = ALGO_BYTES_PER_CELL[sc.model] * sc.cells
+    peak, kind = measured_peak()
+    return {"workload": sc.name, "steps": steps, "us_per_step": dt * 1e6,
+            "cell_updates_per_s": sc.cells / dt, "algorithmic_GBps": algo / dt / 1e9,
+            "frac_of_peak": algo / dt / 1e9 / peak, "peak_kind": kind, "device_status": status}
+
+
 def batched_leg(P, torch, stream, count=256, steps=500):
     """The 256-scenario batch: autotuned launch configuration, then `steps`
     steps in batched launches, vs one launch per scenario per step."""
@@ -395,6 +418,8 @@ def run_gpu(args, sc):
     e2e = None
     if rank == 0 and not args.quick:
         e2e = e2e_run(P, torch, sc, stream, reps=2)
+    if rank == 0 and not args.quick and not args.no_probe:
+        extra["hbm_probe"] = probe_leg(P, torch, stream)
     if rank == 0 and not args.quick and not args.no_batched:
         extra["batched"] = batched_leg(P, torch, stream)
     if rank == 0 and not args.quick and not args.no_serving:
@@ -441,6 +466,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--quick", action="store_true", help="headline only (for profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
