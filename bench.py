@@ -4,12 +4,16 @@ Headline (one JSON line on rank 0): cell-updates/s of the ACO step on the
 2048x2048 grid with 100K agents (50K per side in 64-column bands, rho 0.02),
 one "step" = one synchronous automaton step (proposal, gather resolution,
 move, evaporation + deposit, counters) over the whole grid, inputs resident
-in HBM.  L2 is flushed (a 512 MB write) between timed steps because the
-scenario's working set (~92 MB) would otherwise stay in the 129 MB L2.
+in HBM.  L2 is flushed between timed steps because the scenario's working
+set (~92 MB) would otherwise stay in the 129 MB L2: a 512 MB write, then a
+256 MB read of another buffer, so that the write-backs of the flush's own
+dirty lines happen before the step rather than inside it (the write-only
+flush is reported beside it as `flushed_write_only`).
 
 Also reported on the same line:
-  roofline      fused step kernel: algorithmic bytes (18 B/cell) / kernel time
-                vs the measured HBM copy bandwidth
+  roofline      the step's kernels (propose, stream, resolve): algorithmic
+                bytes (18 B/cell) / step time vs the measured HBM copy
+                bandwidth
   cpu_baseline  the single-threaded CPU oracle on a bounded sample
   e2e           the same metric end to end through the C ABI with host
                 buffers: H2D of the initial state (pinned), the scenario's
@@ -46,9 +50,13 @@ from paper_1412_4933_gb300 import workloads as WL  # noqa: E402
 
 L2_FLUSH_BYTES = 512 << 20
 ALGO_BYTES_PER_CELL = {WL.LEM: 2, WL.ACO: 18}
-KERNEL_SOURCES = ["paper_1412_4933_gb300/csrc/pedsim_kernels.cu",
-                  "paper_1412_4933_gb300/csrc/pedsim_rules.cuh"]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "tiled_step_aco_2048x2048_traffic.md")
+KERNEL_SOURCES = ["paper_1412_4933_gb300/csrc/pedsim_agent.cu",
+                  "paper_1412_4933_gb300/csrc/pedsim_rules.cuh",
+                  "paper_1412_4933_gb300/csrc/pedsim_ptx.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "agent_step_aco_2048x2048_traffic.md")
+# kernels of one step of the default (agent-parallel) variant: proposals,
+# stream, resolution, plus the step-index kernel after every sim_step call
+KERNELS_PER_STEP_CALL = 4
 
 
 def kernel_source_hash() -> str:
@@ -69,7 +77,7 @@ def measured_peak():
 
 
 def recorded_traffic():
-    """Per-step DRAM bytes of the two step kernels from the committed ncu
+    """Per-step DRAM bytes of the step's kernels from the committed ncu
     summary, if it was taken on the current kernel source."""
     try:
         text = open(TRAFFIC_FILE).read()
@@ -361,8 +369,16 @@ def run_gpu(args, sc):
 
     stream = torch.cuda.Stream(device)
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    clean_buf = torch.ones(L2_FLUSH_BYTES // 8, dtype=torch.float32, device=device)
 
     def flush():
+        # write a buffer larger than L2, then read another one so that the
+        # dirty lines of the write are written back before the step starts
+        with torch.cuda.stream(stream):
+            flush_buf.fill_(1.0)
+            clean_buf.sum()
+
+    def flush_write_only():
         with torch.cuda.stream(stream):
             flush_buf.fill_(1.0)
 
@@ -385,9 +401,10 @@ def run_gpu(args, sc):
     value = cells_total / elapsed_max
     ms_per_step = elapsed_max * 1e3 / args.steps
 
-    # roofline of the dominant kernel (fused step): algorithmic bytes / time;
-    # the per-step time also holds the tiny step-index kernel, so this is a
-    # lower bound of the fused kernel's own rate
+    # roofline of the step: algorithmic bytes / time.  The per-step time holds
+    # all of the step's kernels (the streaming pass, which moves the bytes,
+    # overlaps the proposal pass; the resolution pass and the step-index
+    # kernel follow it), so this is a lower bound of the streaming pass's rate
     algo_bytes = ALGO_BYTES_PER_CELL[sc.model] * sc.cells
     peak, peak_kind = measured_peak()
     step_s = elapsed / args.steps
@@ -395,10 +412,17 @@ def run_gpu(args, sc):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": recorded_traffic(),
                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes,
-                "kernel": "propose_tile_kernel<16> + resolve_tile_kernel<16>"}
+                "kernel": "agent_propose_kernel + stream_kernel + agent_resolve_kernel"}
 
     extra = {}
     if rank == 0 and not args.quick:
+        # the same steps with the write-only flush (its write-backs land in
+        # the step)
+        wo = time_steps_flushed(sim, torch, stream, min(args.steps, 100), flush_write_only)
+        wo_s = sum(wo) / len(wo)
+        extra["flushed_write_only"] = {"steps": len(wo), "us_per_step": wo_s * 1e6,
+                                       "cell_updates_per_s": sc.cells / wo_s,
+                                       "algorithmic_GBps": algo_bytes / wo_s / 1e9}
         # steady state: back-to-back steps (graph replays), no flush
         with torch.cuda.stream(stream):
             sim.step(32)
@@ -442,10 +466,13 @@ def run_gpu(args, sc):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": sc.name, "W": sc.W, "H": sc.H, "agents": sc.agents,
                        "model": "ACO" if sc.model else "LEM", "rho": sc.rho, "seed": sc.seed,
-                       "band_cols": sc.band_cols, "l2": "flushed between timed steps (512 MB write)",
+                       "band_cols": sc.band_cols,
+                       "l2": "flushed between timed steps (512 MB write, then a 256 MB read of "
+                             "another buffer)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "clocks": clocks, "gpu_launches": 2 * args.steps, "device_status": status,
+            "clocks": clocks, "gpu_launches": KERNELS_PER_STEP_CALL * args.steps,
+            "device_status": status,
         }
         line.update(extra)
         print(json.dumps(line), flush=True)

@@ -162,7 +162,7 @@ int sim_save(sim_t *s, void *buf, size_t *len);
 int sim_load(sim_t *s, const void *buf, size_t len);
 
 /* Step implementations; all give bit-identical results.
- * PEDSIM_VARIANT_TILED    (default) two kernels per step: TMA-staged
+ * PEDSIM_VARIANT_TILED    two kernels per step: TMA-staged
  *                         proposals of 128 x tile_h tiles into a 1-byte
  *                         proposal plane, then TMA-staged gather resolution
  *                         with streamed pheromone evaporation and deposit
@@ -170,18 +170,27 @@ int sim_load(sim_t *s, const void *buf, size_t len);
  *                         loads (reference baseline of the tiled kernels)
  * PEDSIM_VARIANT_FUSED    one persistent kernel per step over TMA-staged
  *                         tiles with a 3-cell halo (proposals recomputed in
- *                         the halo instead of a proposal plane)
+ *                         the halo instead of a proposal plane); only tiles
+ *                         with an agent in or next to them take the full
+ *                         rule, the others only evaporate
+ * PEDSIM_VARIANT_AGENT    (default) three kernels per step: one thread per agent
+ *                         computes its proposal while every cell's pheromone
+ *                         evaporates in a separate streaming pass; then one
+ *                         thread per agent resolves its target cell and
+ *                         applies the winner's move and deposit
  * Selecting a variant resets the tile shape to its default (tiled: 128 x 16;
- * fused: 64 x 16).                                                            */
+ * fused: 64 x 16; the agent variant has none).                                */
 #define PEDSIM_VARIANT_TILED    0
 #define PEDSIM_VARIANT_TWO_PASS 1
 #define PEDSIM_VARIANT_FUSED    2
+#define PEDSIM_VARIANT_AGENT    3
 int sim_set_variant(sim_t *s, int variant);
 
 /* Tile shape of the current variant: tiled: tile_w = 128, tile_h in
- * {8, 16, 32}; fused: (tile_w, tile_h) in {(32,16), (64,8), (64,16),
+ * {8, 16}; fused: (tile_w, tile_h) in {(32,16), (64,8), (64,16),
  * (128,8), (128,16)} plus CTAs per SM of its persistent grid (0 =
- * automatic; ignored by the tiled variant).  PEDSIM_EINVAL otherwise.        */
+ * automatic; ignored by the tiled variant).  PEDSIM_EINVAL otherwise, and
+ * always for the agent and two-pass variants.                                */
 int sim_set_tiling(sim_t *s, int tile_w, int tile_h, int ctas_per_sm);
 
 /* Sticky device error word of the handle: 0, or PEDSIM_ETIMEDOUT when a
@@ -209,8 +218,8 @@ int sim_batch_step(batch_t *b, int n);
 int sim_batch_stats(batch_t *b, int i, sim_stats_t *out);
 int sim_batch_read_grid(batch_t *b, int i, uint8_t *occ, uint32_t *ids, float *tauA,
                         float *tauB);
-/* Step variant (PEDSIM_VARIANT_TILED or PEDSIM_VARIANT_FUSED) and tile shape
- * of the batched launches (see sim_set_variant / sim_set_tiling).            */
+/* Step variant (PEDSIM_VARIANT_TILED, _FUSED or _AGENT) and tile shape of
+ * the batched launches (see sim_set_variant / sim_set_tiling).               */
 int sim_batch_set_variant(batch_t *b, int variant);
 int sim_batch_set_tiling(batch_t *b, int tile_w, int tile_h, int ctas_per_sm);
 int sim_batch_device_status(batch_t *b);

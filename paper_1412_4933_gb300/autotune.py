@@ -1,9 +1,10 @@
 """Autotuner of the batched step's launch configuration.
 
 Knobs: the step variant (tiled two-kernel step with 128 x 8 or 128 x 16
-tiles, or the fused persistent kernel with one of its tile shapes) and, for
-the persistent kernel, the CTAs per SM (how many tiles, possibly of different
-scenarios, an SM works on at once).  Each candidate is timed on a scratch
+tiles, the fused persistent kernel with one of its tile shapes, or the
+agent-parallel step, which has no tiles) and, for the persistent kernel, the
+CTAs per SM (how many tiles, possibly of different scenarios, an SM works on
+at once).  Each candidate is timed on a scratch
 batch built from the same scenario descriptions (so the tuned batch's own
 state is never advanced), and the winner is cached per (GPU name, size
 class) in a JSON file.  Every candidate gives bit-identical results, so the
@@ -19,6 +20,7 @@ import time
 from . import pedsim as P
 
 CANDIDATES = [
+    (P.VARIANT_AGENT, 0, 0, 0),
     (P.VARIANT_TILED, 128, 8, 0),
     (P.VARIANT_TILED, 128, 16, 0),
     (P.VARIANT_FUSED, 64, 16, 0),
@@ -67,7 +69,8 @@ def _store_cache(cache: dict) -> None:
 def apply(batch, choice) -> None:
     variant, tw, th, cps = choice
     batch.set_variant(variant)
-    batch.set_tiling(tw, th, cps)
+    if variant != P.VARIANT_AGENT:
+        batch.set_tiling(tw, th, cps)
 
 
 def tune(scenarios, steps: int = 16, candidates=CANDIDATES, use_cache: bool = True,

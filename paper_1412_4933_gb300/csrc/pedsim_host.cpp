@@ -24,8 +24,8 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // Device memory layout of one scenario (one allocation)
 // ---------------------------------------------------------------------------
 struct Layout {
-    size_t desc, occ[2], prop, ids, tau[2][2], arrival, tour, part, error, prefix, counts, totals,
-        done;
+    size_t desc, occ[2], prop, ids, tau[2][2], arrival, tour, pos, acode, part, error, prefix,
+        counts, totals, act, act_bytes;
     size_t total;
     uint32_t n_slots;
     bool has_tau, has_tour;
@@ -35,6 +35,14 @@ int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
 // Counter slots: one per tile of the smallest tile shape of any variant, and
 // at least one per CTA of the two-pass variant.
+// Most work items any fused tile shape gives a W x H grid.
+uint32_t fused_max_tiles(int W, int H)
+{
+    const uint32_t a = (uint32_t)ceil_div(W, 32) * (uint32_t)ceil_div(H, 16);
+    const uint32_t b = (uint32_t)ceil_div(W, 64) * (uint32_t)ceil_div(H, 8);
+    return std::max(a, b);
+}
+
 uint32_t counter_slots(int W, int H)
 {
     int n = ceil_div(W, 32) * ceil_div(H, 16);
@@ -67,12 +75,16 @@ Layout make_layout(int W, int H, const sim_params &p)
         for (int q = 0; q < 2; ++q) L.tau[g][q] = L.has_tau ? take(4 * cells) : 0;
     L.arrival = take(4 * agents);
     L.tour = L.has_tour ? take(4 * agents) : 0;
+    L.pos = take(4 * agents);  // cell of each agent (agent-parallel variant)
+    L.acode = take(agents);    // proposal code and group of each agent (same)
     L.part = take(8 * kNumCounters * (size_t)L.n_slots);
     L.error = take(4);
-    L.prefix = take(8);
+    L.prefix = take(3 * 8);  // tile, cell-block and agent-block prefixes of one scenario
     L.counts = take(4 * kGridCounts);
     L.totals = take(8 * kNumCounters);
-    L.done = take(8);  // step ticket and work counter of the fused launch
+    // tile-activity block of the fused step, sized for its smallest tiles
+    L.act_bytes = activity_bytes(std::max(fused_max_tiles(W, H), 1u));
+    L.act = take(L.act_bytes);
     L.total = off;
     return L;
 }
@@ -115,6 +127,15 @@ bool encode_2d(CUtensorMap *map, CUtensorMapDataType type, size_t elem, void *ba
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Marks a work list's activity block invalid: the next fused launch treats
+// every tile as active and rebuilds flags and lists from scratch.
+cudaError_t reset_activity(ActivityCtl *a, size_t bytes, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(a, 0, bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&a->reset, 1, sizeof(a->reset), st);
+    return e;
+}
+
 int device_sms()
 {
     int dev = 0, sms = 0;
@@ -137,12 +158,13 @@ struct sim_s {
     ScenarioDesc *own_desc = nullptr;  // descriptor in this handle's allocation
     ScenarioDesc *d_desc = nullptr;    // where the live descriptor is (own or a work list)
     uint32_t *d_prefix = nullptr;
+    ActivityCtl *d_act = nullptr;  // tile activity of the fused step
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;  // private stream used for graph capture
     unsigned long long step = 0; // host mirror of the device step index
     unsigned long long end_step = ~0ull;
     uint64_t seed = 0;
-    int variant = kVariantPipeline;
+    int variant = kVariantAgent;
     int tile_w = 128, tile_h = 16, ctas_per_sm = 0;
     int sms = 1;
     cudaGraphExec_t graph = nullptr;
@@ -177,6 +199,16 @@ void drop_graph(sim_t *s)
 
 int tiles_of(int n, int t) { return (n + t - 1) / t; }
 
+// Work blocks of the agent-parallel variant.
+uint32_t cell_blocks(int W, int H)
+{
+    return (uint32_t)(((size_t)W * (size_t)H + kCellBlock - 1) / kCellBlock);
+}
+uint32_t agent_blocks(uint32_t n_per_side)
+{
+    return (uint32_t)((2ull * n_per_side + kAgentBlock - 1) / kAgentBlock);
+}
+
 // Fills hdesc (pointers, params, tensor maps for the current tiling) and
 // uploads it with the tile prefix.
 int upload_desc(sim_t *s)
@@ -194,6 +226,8 @@ int upload_desc(sim_t *s)
             d.tau[g][q] = L.has_tau ? reinterpret_cast<float *>(m + L.tau[g][q]) : nullptr;
     d.arrival = reinterpret_cast<uint32_t *>(m + L.arrival);
     d.tour = L.has_tour ? reinterpret_cast<float *>(m + L.tour) : nullptr;
+    d.pos = reinterpret_cast<uint32_t *>(m + L.pos);
+    d.acode = m + L.acode;
     d.part = reinterpret_cast<unsigned long long *>(m + L.part);
     d.n_slots = L.n_slots;
     d.step = s->step;
@@ -226,7 +260,9 @@ int upload_desc(sim_t *s)
             for (int g = 0; g < 2; ++g)
                 for (int q = 0; q < 2; ++q)
                     if (!encode_2d(&d.map_tau[g][q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, d.tau[g][q],
-                                   s->W, s->H, s->tile_w + 8, s->tile_h + 6))
+                                   s->W, s->H, s->tile_w + 8, s->tile_h + 6) ||
+                        !encode_2d(&d.map_tau_tile[g][q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                                   d.tau[g][q], s->W, s->H, s->tile_w, s->tile_h))
                         return fail(s, PEDSIM_ECUDA, "cuTensorMapEncodeTiled failed (pheromone)");
     } else if (s->variant == kVariantPipeline) {
         bool ok = true;
@@ -247,7 +283,8 @@ int upload_desc(sim_t *s)
                                          d.tau[g][q], s->W, s->H, TWd, THd);
         if (!ok) return fail(s, PEDSIM_ECUDA, "cuTensorMapEncodeTiled failed (tiled variant)");
     }
-    const uint32_t prefix[2] = {0u, (uint32_t)(d.tiles_x * d.tiles_y)};
+    const uint32_t prefix[6] = {0u, (uint32_t)(d.tiles_x * d.tiles_y), 0u, cell_blocks(s->W, s->H),
+                                0u, agent_blocks(s->p.n_per_side)};
     // the handle's own descriptor becomes the live one again (a work list that
     // held it re-uploads its copy when it runs next)
     s->d_desc = s->own_desc;
@@ -255,6 +292,8 @@ int upload_desc(sim_t *s)
     // pageable host sources are staged before cudaMemcpyAsync returns
     SIM_CUDA(s, cudaMemcpyAsync(s->d_prefix, prefix, sizeof(prefix), cudaMemcpyHostToDevice,
                                 s->stream));
+    // tiling, state or step changed: the activity flags start over
+    SIM_CUDA(s, reset_activity(s->d_act, s->L.act_bytes, s->stream));
     drop_graph(s);
     return PEDSIM_OK;
 }
@@ -269,7 +308,6 @@ int fused_grid(const sim_t *s, uint32_t total)
 // Launches the kernels of step (step index + t_off) on stream st.
 int launch_one_step(sim_t *s, int t_off, cudaStream_t st)
 {
-    unsigned int *done = reinterpret_cast<unsigned int *>(s->dmem + s->L.done);
     const uint32_t total = (uint32_t)(s->hdesc.tiles_x * s->hdesc.tiles_y);
     if (s->variant == kVariantTwoPass) {
         SIM_CUDA(s, launch_two_pass_step(s->d_desc, s->hdesc.prop, s->W, s->H, t_off, st));
@@ -279,8 +317,14 @@ int launch_one_step(sim_t *s, int t_off, cudaStream_t st)
         SIM_CUDA(s, launch_pipeline_step(s->d_desc, s->d_prefix, 1, total, t_off, s->tile_h, st));
         return PEDSIM_OK;
     }
+    if (s->variant == kVariantAgent) {
+        SIM_CUDA(s, launch_agent_step(s->d_desc, s->d_prefix + 2, s->d_prefix + 4, 1,
+                                      cell_blocks(s->W, s->H), agent_blocks(s->p.n_per_side),
+                                      t_off, st));
+        return PEDSIM_OK;
+    }
     SIM_CUDA(s, launch_fused_step(s->d_desc, s->d_prefix, 1, total, t_off, s->tile_w, s->tile_h,
-                                  fused_grid(s, total), done, st));
+                                  fused_grid(s, total), s->d_act, st));
     return PEDSIM_OK;
 }
 
@@ -359,8 +403,8 @@ static int pedsim_create_on_stream(int W, int H, const sim_params *p, cudaStream
     s->own_desc = reinterpret_cast<ScenarioDesc *>(s->dmem + s->L.desc);
     s->d_desc = s->own_desc;
     s->d_prefix = reinterpret_cast<uint32_t *>(s->dmem + s->L.prefix);
-    if (cudaMemsetAsync(s->dmem + s->L.done, 0, 8, stream) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    s->d_act = reinterpret_cast<ActivityCtl *>(s->dmem + s->L.act);
+    if (cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess) {
         cudaFreeAsync(s->dmem, stream);
         delete s;
         return PEDSIM_ECUDA;
@@ -428,6 +472,7 @@ int sim_place(sim_t *s, uint64_t seed)
     if (rc != PEDSIM_OK) return rc;
     SIM_CUDA(s, launch_init(s->d_desc, 1, s->W * s->H, (int)agents_len(s), s->stream));
     SIM_CUDA(s, launch_place(s->d_desc, 1, s->stream));
+    SIM_CUDA(s, launch_build_pos(s->d_desc, s->W * s->H, s->stream));
     return PEDSIM_OK;
 }
 
@@ -537,6 +582,7 @@ int sim_set_state(sim_t *s, uint64_t seed, uint64_t step, const uint8_t *occ, co
         SIM_CUDA(s, cudaMemcpyAsync(s->hdesc.arrival, arrival, 4 * na, cudaMemcpyHostToDevice, s->stream));
     if (tour && s->L.has_tour)
         SIM_CUDA(s, cudaMemcpyAsync(s->hdesc.tour, tour, 4 * na, cudaMemcpyHostToDevice, s->stream));
+    SIM_CUDA(s, launch_build_pos(s->d_desc, s->W * s->H, s->stream));
     return PEDSIM_OK;
 }
 
@@ -672,7 +718,7 @@ int sim_load(sim_t *s, const void *buf, size_t len)
 int sim_set_variant(sim_t *s, int variant)
 {
     if (!s || (variant != kVariantPipeline && variant != kVariantTwoPass &&
-               variant != kVariantFused))
+               variant != kVariantFused && variant != kVariantAgent))
         return fail(s, PEDSIM_EINVAL, "unknown variant");
     if (variant == s->variant) return PEDSIM_OK;
     s->variant = variant;
@@ -680,13 +726,18 @@ int sim_set_variant(sim_t *s, int variant)
     s->tile_w = variant == kVariantFused ? 64 : 128;
     s->tile_h = 16;
     s->ctas_per_sm = 0;
-    return upload_desc(s);
+    int rc = upload_desc(s);
+    // agent positions are kept up to date by the agent-parallel variant only
+    if (rc == PEDSIM_OK && variant == kVariantAgent)
+        SIM_CUDA(s, launch_build_pos(s->d_desc, s->W * s->H, s->stream));
+    return rc;
 }
 
 int sim_set_tiling(sim_t *s, int tile_w, int tile_h, int ctas_per_sm)
 {
-    const bool ok = s && (s->variant == kVariantFused ? tile_supported(tile_w, tile_h)
-                                                      : pipeline_tile_supported(tile_w, tile_h));
+    const bool ok = s && s->variant != kVariantAgent && s->variant != kVariantTwoPass &&
+                    (s->variant == kVariantFused ? tile_supported(tile_w, tile_h)
+                                                 : pipeline_tile_supported(tile_w, tile_h));
     if (!ok || ctas_per_sm < 0 || ctas_per_sm > 32)
         return fail(s, PEDSIM_EINVAL, "unsupported tile shape");
     s->tile_w = tile_w;
@@ -734,11 +785,13 @@ namespace {
 // the (scenario, tile) work list, and the graph of kGraphSteps steps.
 struct MultiRun {
     ScenarioDesc *d_descs = nullptr;
-    uint32_t *d_prefix = nullptr;
-    unsigned int *d_done = nullptr;  // step ticket of the shared launches
-    int capacity = 0, count = 0;
+    uint32_t *d_prefix = nullptr;  // tile, cell-block and agent-block prefixes (3 x capacity + 1)
+    uint32_t cell_total = 0, agent_total = 0;
+    ActivityCtl *d_act = nullptr;  // tile activity of the shared fused launches
+    size_t act_capacity = 0;       // bytes
+    int capacity = 0, count = 0, prefix_n = 0;
     uint32_t total = 0;
-    int variant = kVariantPipeline;
+    int variant = kVariantAgent;
     int tile_w = 128, tile_h = 16, ctas_per_sm = 0, sms = 1;
     cudaStream_t stream = nullptr, cap = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -763,11 +816,7 @@ struct MultiRun {
                                         sizeof(ScenarioDesc) * (size_t)cap_new, stream);
         if (e == cudaSuccess)
             e = cudaMallocAsync(reinterpret_cast<void **>(&d_prefix),
-                                sizeof(uint32_t) * (size_t)(cap_new + 1), stream);
-        if (e == cudaSuccess && !d_done) {
-            e = cudaMallocAsync(reinterpret_cast<void **>(&d_done), 2 * sizeof(unsigned int), stream);
-            if (e == cudaSuccess) e = cudaMemsetAsync(d_done, 0, 2 * sizeof(unsigned int), stream);
-        }
+                                3 * sizeof(uint32_t) * (size_t)(cap_new + 1), stream);
         if (e != cudaSuccess) return cuda_(e, "work list allocation");
         capacity = cap_new;
         return PEDSIM_OK;
@@ -778,14 +827,32 @@ struct MultiRun {
     {
         int rc = reserve((int)sims.size());
         if (rc) return rc;
-        std::vector<ScenarioDesc> h(sims.size());
-        std::vector<uint32_t> pre(sims.size() + 1, 0);
-        for (size_t i = 0; i < sims.size(); ++i) {
+        const size_t n = sims.size();
+        std::vector<ScenarioDesc> h(n);
+        std::vector<uint32_t> pre(3 * (n + 1), 0);  // tiles, cell blocks, agent blocks
+        for (size_t i = 0; i < n; ++i) {
             h[i] = sims[i]->hdesc;
             pre[i + 1] = pre[i] + (uint32_t)(h[i].tiles_x * h[i].tiles_y);
+            pre[n + 1 + i + 1] = pre[n + 1 + i] + cell_blocks(sims[i]->W, sims[i]->H);
+            pre[2 * (n + 1) + i + 1] = pre[2 * (n + 1) + i] + agent_blocks(sims[i]->p.n_per_side);
         }
-        count = (int)sims.size();
-        total = pre.back();
+        count = (int)n;
+        total = pre[n];
+        cell_total = pre[2 * n + 1];
+        agent_total = pre[3 * n + 2];
+        const size_t need = activity_bytes(std::max(total, 1u));
+        if (need > act_capacity) {
+            if (d_act) cudaFreeAsync(d_act, stream);
+            d_act = nullptr;
+            act_capacity = 0;
+            cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d_act), 2 * need, stream);
+            if (e != cudaSuccess) return cuda_(e, "activity block allocation");
+            act_capacity = 2 * need;
+        }
+        {
+            cudaError_t e = reset_activity(d_act, need, stream);
+            if (e != cudaSuccess) return cuda_(e, "activity block reset");
+        }
         for (size_t i = 0; i < sims.size(); ++i) h[i].step = sims[i]->step;  // exact host mirror
         if (count) {
             cudaError_t e = cudaMemcpyAsync(d_descs, h.data(), sizeof(ScenarioDesc) * h.size(),
@@ -793,6 +860,7 @@ struct MultiRun {
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(d_prefix, pre.data(), sizeof(uint32_t) * pre.size(),
                                     cudaMemcpyHostToDevice, stream);
+            prefix_n = (int)n;
             if (e != cudaSuccess) return cuda_(e, "work list upload");
         }
         // the array now holds the live descriptors (and step indices) of these
@@ -811,12 +879,16 @@ struct MultiRun {
 
     int launch_steps(int k, cudaStream_t st)
     {
+        const int n = prefix_n;
         for (int i = 0; i < k; ++i) {
-            cudaError_t e = variant == kVariantFused
-                                ? launch_fused_step(d_descs, d_prefix, count, total, i, tile_w,
-                                                    tile_h, grid(), d_done, st)
-                                : launch_pipeline_step(d_descs, d_prefix, count, total, i, tile_h,
-                                                       st);
+            cudaError_t e =
+                variant == kVariantFused
+                    ? launch_fused_step(d_descs, d_prefix, count, total, i, tile_w, tile_h, grid(),
+                                        d_act, st)
+                : variant == kVariantAgent
+                    ? launch_agent_step(d_descs, d_prefix + (n + 1), d_prefix + 2 * (n + 1), count,
+                                        cell_total, agent_total, i, st)
+                    : launch_pipeline_step(d_descs, d_prefix, count, total, i, tile_h, st);
             if (e != cudaSuccess) return cuda_(e, "batched step launch");
         }
         cudaError_t e = launch_advance(d_descs, count, k, st);
@@ -855,10 +927,11 @@ struct MultiRun {
         drop();
         if (d_descs) cudaFreeAsync(d_descs, stream);
         if (d_prefix) cudaFreeAsync(d_prefix, stream);
-        if (d_done) cudaFreeAsync(d_done, stream);
+        if (d_act) cudaFreeAsync(d_act, stream);
         d_descs = nullptr;
         d_prefix = nullptr;
-        d_done = nullptr;
+        d_act = nullptr;
+        act_capacity = 0;
         if (cap) cudaStreamDestroy(cap);
         cap = nullptr;
     }
@@ -959,8 +1032,9 @@ int sim_batch_read_grid(batch_t *b, int i, uint8_t *occ, uint32_t *ids, float *t
 int sim_batch_set_tiling(batch_t *b, int tile_w, int tile_h, int ctas_per_sm)
 {
     if (!b) return PEDSIM_EINVAL;
-    const bool ok = b->run.variant == kVariantFused ? tile_supported(tile_w, tile_h)
-                                                    : pipeline_tile_supported(tile_w, tile_h);
+    const bool ok = b->run.variant != kVariantAgent &&
+                    (b->run.variant == kVariantFused ? tile_supported(tile_w, tile_h)
+                                                     : pipeline_tile_supported(tile_w, tile_h));
     if (!ok || ctas_per_sm < 0 || ctas_per_sm > 32) return PEDSIM_EINVAL;
     for (sim_t *s : b->sims) {
         int rc = retile(s, b->run.variant, tile_w, tile_h, ctas_per_sm);
@@ -974,11 +1048,17 @@ int sim_batch_set_tiling(batch_t *b, int tile_w, int tile_h, int ctas_per_sm)
 
 int sim_batch_set_variant(batch_t *b, int variant)
 {
-    if (!b || (variant != kVariantPipeline && variant != kVariantFused)) return PEDSIM_EINVAL;
+    if (!b || (variant != kVariantPipeline && variant != kVariantFused &&
+               variant != kVariantAgent))
+        return PEDSIM_EINVAL;
     b->run.variant = variant;
     const int tw = variant == kVariantFused ? 64 : 128;
     for (sim_t *s : b->sims) {
         int rc = retile(s, variant, tw, 16, 0);
+        if (rc == PEDSIM_OK && variant == kVariantAgent) {
+            cudaError_t e = launch_build_pos(s->d_desc, s->W * s->H, s->stream);
+            if (e != cudaSuccess) rc = cuda_fail(s, e, "position rebuild");
+        }
         if (rc) { b->run.err = s->err; return rc; }
     }
     b->run.tile_w = tw;

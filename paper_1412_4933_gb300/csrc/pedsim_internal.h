@@ -32,6 +32,11 @@ namespace pedsim {
 //                 crossed[B]) x n_slots: each tile (or CTA) adds its counts to
 //                 its own slot, so no two writers share an address; totals
 //                 are the slot sums
+//   pos           uint32 cell index of every agent, indexed by id (agent-
+//                 parallel variant; rebuilt from the planes whenever the
+//                 state is set from outside it)
+//   acode         uint8 per agent: proposal code | group << 4 of the current
+//                 step (agent-parallel variant)
 constexpr int kDescHeaderBytes = 256;
 
 struct alignas(128) ScenarioDesc {
@@ -57,21 +62,45 @@ struct alignas(128) ScenarioDesc {
     float *tour;
     unsigned long long *part;
     int *error;
-    uint8_t header_pad_[kDescHeaderBytes - 96 - 12 * 8];
+    uint32_t *pos;
+    uint8_t *acode;
+    uint8_t header_pad_[kDescHeaderBytes - 96 - 14 * 8];
     // TMA tensor maps; boxes follow the variant and tile shape:
     //   tiled two-kernel step: occ (tile_w + 32) x (tile_h + 2), occ_out and
     //   prop_out tile_w x tile_h, prop (tile_w + 32) x (tile_h + 4), tau
     //   tile_w x tile_h (loads and stores);
     //   fused step: occ (tile_w + 32) x (tile_h + 6), tau (tile_w + 8) x
-    //   (tile_h + 6).
+    //   (tile_h + 6), tau_tile tile_w x tile_h (quiet tiles).
     CUtensorMap map_occ[2];
     CUtensorMap map_occ_out[2];
     CUtensorMap map_prop;
     CUtensorMap map_prop_out;
-    CUtensorMap map_tau[2][2];   // [group][parity]
+    CUtensorMap map_tau[2][2];       // [group][parity]
+    CUtensorMap map_tau_tile[2][2];  // [group][parity]
 };
-static_assert(sizeof(ScenarioDesc) == kDescHeaderBytes + 10 * sizeof(CUtensorMap),
+static_assert(sizeof(ScenarioDesc) == kDescHeaderBytes + 14 * sizeof(CUtensorMap),
               "descriptor header layout");
+
+// Tile-activity control block of one work list of the fused step (device
+// memory).  It is followed by flags[3][ceil(total / 32)] (one bit per work
+// item) and list[3][total] (work item indices), total being the work list's
+// item count.  Launch k uses generation g = phase: flags[g] marks the active
+// tiles and list[g][0 .. n_act[g]) enumerates them; it sets generation
+// (g + 1) % 3 for the next launch and clears (g + 2) % 3.  All zero except
+// `reset` = nonzero after the host changes the work list or a state: that
+// launch treats every tile as active.
+struct ActivityCtl {
+    uint32_t ticket;    // elects the launch's last CTA
+    uint32_t work;      // next entry of the active list to hand out
+    uint32_t phase;     // launch index mod 3
+    uint32_t reset;
+    uint32_t n_act[3];
+    uint32_t work_nat;  // next work item of the natural-order pass
+};
+inline size_t activity_bytes(uint32_t total)
+{
+    return sizeof(ActivityCtl) + 4 * (3 * (((size_t)total + 31) / 32) + 3 * (size_t)total);
+}
 
 // Counter slots.
 enum { kMoved = 0, kConflicts = 1, kCrossedA = 2, kCrossedB = 3, kNumCounters = 4 };
@@ -80,7 +109,12 @@ enum { kMoved = 0, kConflicts = 1, kCrossedA = 2, kCrossedB = 3, kNumCounters = 
 enum { kGridCounts = 4 };
 
 // Step-kernel variants.
-enum { kVariantPipeline = 0, kVariantTwoPass = 1, kVariantFused = 2 };
+enum { kVariantPipeline = 0, kVariantTwoPass = 1, kVariantFused = 2, kVariantAgent = 3 };
+
+// Work units of the agent-parallel variant: cells per CTA of its streaming
+// pass, agents per CTA of its proposal and resolution passes.
+constexpr int kCellBlock = 4096;
+constexpr int kAgentBlock = 256;
 
 // Supported fused tile shapes (tile_w x tile_h).
 bool tile_supported(int tile_w, int tile_h);
@@ -94,11 +128,10 @@ cudaError_t launch_init(const ScenarioDesc *d_descs, int n, int max_cells, int m
 cudaError_t launch_place(const ScenarioDesc *d_descs, int n, cudaStream_t stream);
 // One fused step (t = step + t_off) over all (scenario, tile) items;
 // tile_prefix[i] = first work item of scenario i, tile_prefix[n] = total.
-// `done` points at two device words, zero between launches: a ticket that
-// elects the last CTA and the dynamic work-item counter it re-arms.
+// `act` is the work list's activity block (activity_bytes(total) bytes).
 cudaError_t launch_fused_step(const ScenarioDesc *d_descs, const uint32_t *d_tile_prefix,
                               int n, uint32_t total_tiles, int t_off, int tile_w, int tile_h,
-                              int grid, unsigned int *done, cudaStream_t stream);
+                              int grid, ActivityCtl *act, cudaStream_t stream);
 // Tiled two-kernel step (K1 proposals, K2 resolution) over all (scenario,
 // tile) items; tiles are 128 x tile_h.
 bool pipeline_tile_supported(int tile_w, int tile_h);
@@ -109,6 +142,14 @@ cudaError_t launch_pipeline_step(const ScenarioDesc *d_descs, const uint32_t *d_
 int two_pass_grid(int W, int H);
 cudaError_t launch_two_pass_step(const ScenarioDesc *d_desc, uint8_t *d_prop, int W, int H,
                                  int t_off, cudaStream_t stream);
+// Agent-parallel step over scenarios [0, n): cell_prefix[i] / agent_prefix[i]
+// = first streaming / agent CTA of scenario i (ceil(W*H / kCellBlock) and
+// ceil(2 n_per_side / kAgentBlock) per scenario), [n] = the totals.
+cudaError_t launch_agent_step(const ScenarioDesc *d_descs, const uint32_t *d_cell_prefix,
+                              const uint32_t *d_agent_prefix, int n, uint32_t cell_blocks,
+                              uint32_t agent_blocks, int t_off, cudaStream_t stream);
+// Rebuilds pos[] of one scenario from its planes at its current step.
+cudaError_t launch_build_pos(const ScenarioDesc *d_desc, int cells, cudaStream_t stream);
 // step += k (clamped at end_step) for scenarios [0, n).
 cudaError_t launch_advance(const ScenarioDesc *d_descs, int n, int k, cudaStream_t stream);
 // out[0..3] = counter totals of one scenario (sums over its slots).

@@ -4,133 +4,36 @@
 //                      counters
 //   place_kernel       random placement in the edge bands (Sec. IV.a)
 //   fused_step_kernel  one synchronous step (Sec. IV.b-d) in a single pass:
-//                      persistent CTAs walk the (scenario, tile) work list;
-//                      per tile a TMA copy stages the occupancy tile with a
-//                      3-cell halo (16 columns either side, for the 16-byte
-//                      TMA rule) and the two pheromone tiles in shared memory,
-//                      double-buffered behind mbarriers; proposals of the tile
-//                      plus a 2-cell ring are computed into shared memory, then
-//                      every tile cell resolves (gather), evaporates (Eq. 3),
-//                      deposits (Eq. 4/5) and counts
+//                      persistent CTAs (four consumer warps and a producer
+//                      warp) walk the (scenario, tile) work list, tiles near
+//                      agents first; for such a tile a TMA copy stages the
+//                      occupancy with a 3-cell halo and the two pheromone tiles
+//                      in shared memory (two stages behind mbarriers), the
+//                      proposals of the tile plus a 2-cell ring are computed,
+//                      then every tile cell resolves (gather), evaporates
+//                      (Eq. 3), deposits (Eq. 4/5) and counts; a tile with no
+//                      agent within reach only evaporates its pheromone
+//   propose_tile_kernel + resolve_tile_kernel
+//                      the same step as two kernels per tile through a
+//                      proposal plane
 //   propose_plane_kernel + resolve_plane_kernel
 //                      the same step in two passes through a proposal plane in
 //                      HBM (baseline and cross-check of the fused pass)
 //   grid_counts_kernel agents / parked per group (read-back helper)
-// The last CTA of each step's final kernel advances the step index.
+// advance_kernel adds the step count of a launch group to every step index.
 #include "pedsim_internal.h"
 #include "pedsim_rules.cuh"
+#include "pedsim_ptx.cuh"
 
 namespace pedsim {
 
 constexpr int kThreads = 256;
-constexpr int kErrTimeout = -110;
-// A bounded wait gives up after this many SM clock cycles (about 2 s at the
-// 2.07 GHz maximum clock).
-constexpr long long kWaitCycles = 4000000000ll;
-
-// ---------------------------------------------------------------------------
-// PTX helpers: mbarrier and TMA (cp.async.bulk.tensor)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-// Waits for the phase with the given parity; false after kWaitCycles.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
-{
-    const long long start = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - start > kWaitCycles) return false;
-    }
-    return true;
-}
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
-                                            uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// Programmatic dependent launch: wait until the preceding kernel in the
-// stream has completed and its memory is visible (no-op when the launch did
-// not overlap), and let the next kernel start its prologue.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
-
-// Starts fetching a tensor map (kept in global memory) into the TMA unit's
-// descriptor cache, so that the copy issued later does not wait for it.
-__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map)
-{
-    asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
-}
-
-// Shared -> global tiled bulk copy (elements outside the tensor are skipped).
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, const void *src)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map),
-        "r"(x), "r"(y), "r"(smem_u32(src))
-        : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-
-// Waits until every committed bulk store has finished reading shared memory.
-__device__ __forceinline__ void bulk_wait_read()
-{
-    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async_smem()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_mbarrier_init()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
 // ---------------------------------------------------------------------------
 // Shared per-cell resolution (Sec. IV.d), used by both step variants.
 // occ_at(dx, dy): occupancy at t; prop_at(dx, dy): proposal code at t.
 // Returns the occupancy byte at t+1 and reports the group of an agent that
 // entered this cell (0 if none) plus the deposit it leaves.
 // ---------------------------------------------------------------------------
-struct Counts {
-    unsigned moved = 0, conflicts = 0, crossed_a = 0, crossed_b = 0;
-};
 
 template <class OccFn, class PropFn>
 __device__ __forceinline__ int resolve_cell(const ScenarioDesc &d, int x, int y, uint64_t cell,
@@ -172,24 +75,6 @@ __device__ __forceinline__ int resolve_cell(const ScenarioDesc &d, int x, int y,
         x + dx, y + dy, W, H, cell + (int64_t)dy * W + dx, t, d.seed,
         [&](int ex, int ey) { return prop_at(dx + ex, dy + ey); }, &k);
     return (w == 8 - code) ? 0 : o;
-}
-
-// Adds the warp's counts to counter slot `slot` of the scenario (warp-shuffle
-// reduction; each tile or CTA owns its slot, so the adds never contend).
-__device__ __forceinline__ void flush_counts(const ScenarioDesc &d, Counts &c, uint32_t slot)
-{
-    const unsigned m = __reduce_add_sync(0xffffffffu, c.moved);
-    const unsigned k = __reduce_add_sync(0xffffffffu, c.conflicts);
-    const unsigned a = __reduce_add_sync(0xffffffffu, c.crossed_a);
-    const unsigned b = __reduce_add_sync(0xffffffffu, c.crossed_b);
-    if ((threadIdx.x & 31) == 0 && (m | k | a | b)) {
-        unsigned long long *ps = d.part + (size_t)slot * kNumCounters;
-        if (m) atomicAdd(&ps[kMoved], (unsigned long long)m);
-        if (k) atomicAdd(&ps[kConflicts], (unsigned long long)k);
-        if (a) atomicAdd(&ps[kCrossedA], (unsigned long long)a);
-        if (b) atomicAdd(&ps[kCrossedB], (unsigned long long)b);
-    }
-    c = Counts{};
 }
 
 // ---------------------------------------------------------------------------
@@ -324,8 +209,67 @@ __global__ void __launch_bounds__(1024) place_kernel(const ScenarioDesc *__restr
     }
 }
 
+// Appends `n` entries of this thread to a shared list with one shared atomic
+// per warp; returns the first slot of this thread.  All 32 lanes must call.
+__device__ __forceinline__ int warp_reserve(unsigned int *counter, int n)
+{
+    const int lane = threadIdx.x & 31;
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned int base = 0;
+    if (lane == 31 && total) base = atomicAdd(counter, (unsigned int)total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return (int)base + incl - n;
+}
+
+// Forward-first part of a proposal (Sec. III): 0 for an agent on its goal
+// column, the forward code when the forward cell is in the grid and empty,
+// -1 when the agent is blocked and needs the full rule.
+template <class OccFn>
+__device__ __forceinline__ int forward_first(int x, int y, int g, int W, int H, OccFn occ)
+{
+    if ((g == 1 && x == W - 1) || (g == 2 && x == 0)) return 0;
+    const int code = kFrameCode[g - 1][1];
+    const int dx = kCodeDX[code];
+    const int nx = x + dx;
+    if ((unsigned)nx < (unsigned)W && occ(dx, 0) == 0) return code;
+    (void)y;
+    (void)H;
+    return -1;
+}
+
 // ---------------------------------------------------------------------------
-// Fused single-pass step
+// Fused single-pass step with tile activity tracking
+//
+// A tile is ACTIVE at a step when an agent stands in it or on a cell next to
+// it: only then can one of its cells change occupancy or receive a deposit
+// (agents move at most one cell per step, Sec. III).  Every other tile is
+// QUIET: its pheromone only evaporates (Eq. 3) and its occupancy stays empty.
+// An active tile that ends the step with agents marks itself and each
+// neighbouring tile that one of those agents touches (its border rows and
+// columns, its corner cells) active for the next step; a mark sets the
+// tile's flag bit and the first mark appends the tile to the next step's
+// list.  Quiet tiles never end a step with agents, so the marks are complete.
+//
+// Per work list (one scenario or a batch) an ActivityCtl block holds three
+// generations of flags and lists; launch k reads generation k % 3, writes
+// k + 1 and clears k + 2.  Work items of a launch: the active list first
+// (dense tiles start at once instead of forming the tail), then every tile
+// in natural order in chunks of kQuietChunk, where flagged tiles are skipped
+// and the rest are quiet.  After the host changes a work list or a state it
+// sets `reset`: that launch treats every tile as active.
+//
+// CTA organisation: four consumer warps work on one item at a time; a fifth,
+// producer, warp claims and decodes work items and issues the TMA copies of
+// an active tile into one of two shared-memory stages (full / empty
+// mbarriers), so claims, list reads and copies overlap the consumers' work.
+// Quiet chunks need no copy: the consumers stream their pheromone through
+// registers, every load of the chunk in flight at once.
 //
 // Shared memory of one CTA.  The byte planes use the occupancy tile's column
 // mapping (column cx <-> x = x0 - 16 + cx, row stride OW), so one index
@@ -338,14 +282,21 @@ __global__ void __launch_bounds__(1024) place_kernel(const ScenarioDesc *__restr
 //                                          y0-1 .. y0+TH
 //   agents         list of the occupied cells of the tile and its 2-ring
 //   moves          list of the tile cells that receive an agent
-//   dep            TH x TW float deposit left in each receiving cell (ACO)
+//   dep            TH x TW float deposit left in each receiving cell (ACO);
+//                  before that, the list of blocked agents, then the list of
+//                  cells with two or more claimants
 // A claim mask holds bit j when the neighbour at scan offset j chose the
 // cell; bitwise OR makes it independent of the order claims arrive in.  The
 // winner byte is (scan index + 1) | 0x10 when there were >= 2 claimants.
 // List order never matters: every list entry's effects are independent.
 // ---------------------------------------------------------------------------
-constexpr int kFusedThreads = 128;
+constexpr int kFusedConsumers = 128;                  // threads working on a tile
+constexpr int kFusedThreads = kFusedConsumers + 32;   // + the producer warp
+constexpr int kStages = 2;
+constexpr int kFusedMinBlocks = 4;  // resident CTAs per SM the register budget allows
 constexpr int align_to(int v, int a) { return (v + a - 1) / a * a; }
+
+enum : uint32_t { kItemEnd = 0, kItemQuiet = 1, kItemActive = 2 };
 
 template <int TW, int TH>
 struct FusedLayout {
@@ -360,20 +311,29 @@ struct FusedLayout {
     static constexpr int WIN_BYTES = align_to((TH + 2) * OW, 16);
     static constexpr int MAX_AGENTS = (TH + 4) * (TW + 4);
     static constexpr int MAX_MOVES = TH * TW;
-    static constexpr int OFF_TAU = 2 * OCC_BYTES;  // [stage][group]
-    static constexpr int OFF_PROP = OFF_TAU + 4 * TAU_BYTES;
+    static constexpr int MAX_CONFLICTS = (TH + 2) * (TW + 2);
+    static constexpr int OFF_TAU = kStages * OCC_BYTES;  // [stage][group]
+    static constexpr int OFF_PROP = OFF_TAU + kStages * 2 * TAU_BYTES;
     static constexpr int OFF_WIN = OFF_PROP + PROP_BYTES;
     static constexpr int OFF_DEP = OFF_WIN + WIN_BYTES;
     static constexpr int OFF_AGENTS = OFF_DEP + TH * TW * 4;
     static constexpr int OFF_MOVES = OFF_AGENTS + align_to(MAX_AGENTS * 2, 16);
-    static constexpr int OFF_MISC = OFF_MOVES + align_to(MAX_MOVES * 2, 16);  // counters, item
-    static constexpr int OFF_BAR = OFF_MISC + 16;  // misc: 4 words
-    static constexpr int SMEM = OFF_BAR + 16 + 128;  // + slack to align the base
+    static constexpr int OFF_MISC = OFF_MOVES + align_to(MAX_MOVES * 2, 16);  // list counters
+    static constexpr int OFF_ITEM = OFF_MISC + 32;           // per stage: item, scenario|mask, kind
+    static constexpr int OFF_BAR = OFF_ITEM + kStages * 16;  // full[stage], empty[stage]
+    static constexpr int SMEM = OFF_BAR + 2 * kStages * 8 + 128;  // + slack to align the base
     // 32-bit word columns covering cx = 12 .. TW+19 (x0-4 .. x0+TW+3)
     static constexpr int WC0 = 3, NWC = TW / 4 + 2;
     static_assert(OW <= 256 && OH <= 256 && TWH <= 256 && THH <= 256, "TMA box limit");
     static_assert((TH + 6) * OW < 65536, "16-bit list entries");
+    static_assert(MAX_AGENTS * 2 <= TH * TW * 4 && MAX_CONFLICTS * 2 <= TH * TW * 4,
+                  "blocked and conflict lists fit the deposit array");
 };
+
+// Tiles per quiet work item: about 2048 cells, so that each consumer thread
+// keeps 16 pheromone cells of both groups in flight.
+template <int TW, int TH>
+__host__ __device__ constexpr int quiet_chunk() { return TW * TH >= 2048 ? 1 : 2048 / (TW * TH); }
 
 __device__ __forceinline__ int scenario_of(const uint32_t *__restrict__ prefix, int n,
                                            uint32_t item)
@@ -386,32 +346,40 @@ __device__ __forceinline__ int scenario_of(const uint32_t *__restrict__ prefix, 
     return lo;
 }
 
-// Called by every CTA of the fused kernel as its last action: the last CTA
-// to arrive re-arms the ticket (ctr[0]) and the dynamic work counter (ctr[1])
-// for the next launch.
-__device__ __forceinline__ void finish_launch(unsigned int *ctr)
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned int ticket = atomicAdd(&ctr[0], 1u);
-        if (ticket == gridDim.x - 1) {
-            atomicExch(&ctr[1], 0u);
-            atomicExch(&ctr[0], 0u);
-            __threadfence();
-        }
-    }
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Barrier 1 over the consumer warps only (the producer warp never joins).
+__device__ __forceinline__ void consumer_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(kFusedConsumers) : "memory");
+}
+
+__device__ __forceinline__ bool consumer_sync_and(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kFusedConsumers)
+        : "memory");
+    return r != 0;
 }
 
 // Per-agent bookkeeping of one move into `cell` from `src` (Sec. IV.d): the
 // id follows the agent, Eq. 5 extends the tour length, the first entry into
 // the opposite band is recorded (Sec. VI).  Returns the deposit's float bits
 // in the low word and 1 << 32 when the agent crossed at this step.
-__device__ __forceinline__ uint64_t apply_move(const ScenarioDesc &d, uint64_t cell,
-                                               uint64_t src, int inc, int xc, bool diagonal,
-                                               uint64_t t)
+// `id` is the moving agent's id, read from its source cell.
+__device__ __forceinline__ uint64_t apply_move_id(const ScenarioDesc &d, uint64_t cell,
+                                                  uint32_t id, int inc, int xc, bool diagonal,
+                                                  uint64_t t)
 {
-    const uint32_t id = d.ids[src];
     d.ids[cell] = id;
     float dep = d.deposit;
     if (d.model == 1 && d.deposit_mode == 1) {
@@ -428,334 +396,597 @@ __device__ __forceinline__ uint64_t apply_move(const ScenarioDesc &d, uint64_t c
     return crossed | (uint64_t)__float_as_uint(dep);
 }
 
+__device__ __forceinline__ uint64_t apply_move(const ScenarioDesc &d, uint64_t cell,
+                                               uint64_t src, int inc, int xc, bool diagonal,
+                                               uint64_t t)
+{
+    return apply_move_id(d, cell, d.ids[src], inc, xc, diagonal, t);
+}
+
 template <int TW, int TH>
-__global__ void __launch_bounds__(kFusedThreads)
+__global__ void __launch_bounds__(kFusedThreads, kFusedMinBlocks)
 fused_step_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__restrict__ tile_prefix,
-                  int n_scen, uint32_t total, int t_off, unsigned int *__restrict__ ctr)
+                  int n_scen, uint32_t total, int t_off, ActivityCtl *__restrict__ act)
 {
     using Lay = FusedLayout<TW, TH>;
-    constexpr int NT = kFusedThreads;
+    constexpr int NT = kFusedConsumers;
     constexpr int OW = Lay::OW, NWC = Lay::NWC, WC0 = Lay::WC0, TWH = Lay::TWH;
     constexpr int GW = TW / 4;  // 4-cell groups per tile row
+    constexpr int QC = quiet_chunk<TW, TH>();
+    constexpr int QG = (TH * GW + NT - 1) / NT;  // 4-cell groups per thread per quiet tile
+    static_assert(32 % QC == 0, "quiet chunks never straddle a flag word");
     extern __shared__ __align__(128) uint8_t smem_raw[];
     // TMA destinations need 128-byte alignment: align the base explicitly
     uint8_t *const smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     uint8_t *const Pp = smem + Lay::OFF_PROP;
     uint8_t *const Cw = smem + Lay::OFF_WIN;
     float *const depv = reinterpret_cast<float *>(smem + Lay::OFF_DEP);
+    uint16_t *const blocked = reinterpret_cast<uint16_t *>(smem + Lay::OFF_DEP);
+    uint16_t *const conflicts = reinterpret_cast<uint16_t *>(smem + Lay::OFF_DEP);
     uint16_t *const agents = reinterpret_cast<uint16_t *>(smem + Lay::OFF_AGENTS);
     uint16_t *const moves = reinterpret_cast<uint16_t *>(smem + Lay::OFF_MOVES);
     unsigned int *const misc = reinterpret_cast<unsigned int *>(smem + Lay::OFF_MISC);
-    // misc[0] agents in the list, misc[1] moves in the list, misc[2] next item
-    uint64_t *const bar = reinterpret_cast<uint64_t *>(smem + Lay::OFF_BAR);
+    // misc[0] agents, misc[1] moves, misc[2] blocked agents, misc[3] conflicts,
+    // misc[4] neighbourhood mark bits
+    uint32_t *const item_hdr = reinterpret_cast<uint32_t *>(smem + Lay::OFF_ITEM);
+    uint64_t *const full = reinterpret_cast<uint64_t *>(smem + Lay::OFF_BAR);
+    uint64_t *const empty = full + kStages;
     auto occ_stage = [&](int st) { return smem + st * Lay::OCC_BYTES; };
     auto tau_stage = [&](int st, int g) {
         return reinterpret_cast<float *>(smem + Lay::OFF_TAU + (st * 2 + g) * Lay::TAU_BYTES);
     };
 
+    // This launch's generation of the activity flags and lists.
+    const uint32_t ph = act->phase;
+    const bool all_active = act->reset != 0;
+    const uint32_t n_act = all_active ? 0u : act->n_act[ph];
+    const uint32_t nfw = (total + 31u) / 32u;
+    uint32_t *const flag_base = reinterpret_cast<uint32_t *>(act + 1);
+    const uint32_t *const F_cur = flag_base + ph * nfw;
+    uint32_t *const F_next = flag_base + ((ph + 1u) % 3u) * nfw;
+    uint32_t *const F_old = flag_base + ((ph + 2u) % 3u) * nfw;
+    uint32_t *const list_base = flag_base + 3u * nfw;
+    const uint32_t *const L_cur = list_base + ph * total;
+    uint32_t *const L_next = list_base + ((ph + 1u) % 3u) * total;
+    unsigned int *const n_next = &act->n_act[(ph + 1u) % 3u];
+
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kFusedConsumers / 32);
+        }
         fence_mbarrier_init();
     }
-
-    // Issues the TMA copies of one work item into a stage (thread 0 only).
-    auto issue = [&](uint32_t item, int st) {
-        const int s = scenario_of(tile_prefix, n_scen, item);
-        const ScenarioDesc *d = descs + s;
-        const uint64_t t = d->step + (uint64_t)t_off;
-        if (t >= d->end_step) return;
-        const uint32_t local = item - __ldg(tile_prefix + s);
-        const int ty = (int)(local / (uint32_t)d->tiles_x), tx = (int)(local % (uint32_t)d->tiles_x);
-        const int p = (int)(t & 1);
-        const bool aco = d->model == 1;
-        mbar_arrive_expect_tx(&bar[st], Lay::OH * OW + (aco ? 2 * Lay::TAU_BOX_BYTES : 0));
-        tma_load_2d(occ_stage(st), &d->map_occ[p], tx * TW - 16, ty * TH - 3, &bar[st]);
-        if (aco) {
-            tma_load_2d(tau_stage(st, 0), &d->map_tau[0][p], tx * TW - 4, ty * TH - 3, &bar[st]);
-            tma_load_2d(tau_stage(st, 1), &d->map_tau[1][p], tx * TW - 4, ty * TH - 3, &bar[st]);
-        }
-    };
-
-    // Work items are taken dynamically (ctr[1]) so that tiles crowded with
-    // agents do not pile up on a few CTAs.  Indices are claimed one item
-    // ahead of the prefetch so that the atomic's latency never sits on the
-    // critical path: while item i is computed, item i+1 is being copied and
-    // the index of item i+2 is in flight.
-    if (threadIdx.x == 0) {
-        const uint32_t first = atomicAdd(&ctr[1], 1u);
-        const uint32_t second = atomicAdd(&ctr[1], 1u);
-        misc[2] = first;
-        misc[3] = second;
-        if (first < total) issue(first, 0);
-    }
     __syncthreads();
-    uint32_t item = misc[2];
-    uint32_t next = misc[3];
 
-    Counts cnt;
-    uint32_t phase_bits = 0;
-    int st = 0;
-    const int lane = threadIdx.x & 31;
-    while (item < total) {
-        uint32_t next2 = 0xFFFFFFFFu;
-        if (threadIdx.x == 0) {
-            misc[0] = 0;
-            misc[1] = 0;
-            if (next < total) {
-                fence_proxy_async_smem();
-                issue(next, st ^ 1);
-                next2 = atomicAdd(&ctr[1], 1u);  // consumed at the end of this item
-            } else {
-                next2 = total;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    bool failed = false;
+
+    if (warp == kFusedConsumers / 32) {
+        // ------------------------------ producer ------------------------------
+        auto live = [&](uint32_t sc) {
+            const ScenarioDesc *d = descs + sc;
+            return d->step + (uint64_t)t_off < d->end_step;
+        };
+        bool list_left = n_act > 0;
+        uint32_t pend_j0 = 0, pend_m = 0;  // quiet tiles of a claimed chunk not yet handed out
+        // Next work item with work: an active tile (item, aux = its scenario)
+        // or quiet tiles of one scenario within a chunk (item = the chunk's
+        // first item, aux = scenario << 8 | bit q for each quiet tile item + q).
+        // The natural-order pass also clears generation k + 2's flag words.
+        auto quiet_group = [&](uint32_t &item, uint32_t &aux) {
+            // the first pending tile's scenario and every pending tile of it
+            const int q0 = __ffs(pend_m) - 1;
+            const uint32_t sc = (uint32_t)scenario_of(tile_prefix, n_scen, pend_j0 + (uint32_t)q0);
+            const uint32_t end = __ldg(tile_prefix + sc + 1);
+            uint32_t m = 0;
+            for (int q = q0; q < QC; ++q)
+                if (((pend_m >> q) & 1u) && pend_j0 + (uint32_t)q < end) m |= 1u << q;
+            pend_m &= ~m;
+            item = pend_j0;
+            aux = (sc << 8) | m;
+        };
+        auto claim = [&](uint32_t &item, uint32_t &aux) -> uint32_t {
+            if (pend_m) {
+                quiet_group(item, aux);
+                return kItemQuiet;
             }
-        }
-
-        const int s = scenario_of(tile_prefix, n_scen, item);
-        const ScenarioDesc &d = descs[s];
-        const uint64_t t = d.step + (uint64_t)t_off;
-        const bool active = t < d.end_step;  // uniform: nothing was issued otherwise
-        bool ok = true;
-        if (active) {
-            ok = mbar_wait_bounded(&bar[st], (phase_bits >> st) & 1u);
-            phase_bits ^= 1u << st;
-        }
-        if (!__syncthreads_and(ok)) {
-            if (threadIdx.x == 0) atomicExch(d.error, kErrTimeout);
-            // give a copy still in flight for the next item a bounded chance to
-            // land before the CTA leaves
-            if (next < total) (void)mbar_wait_bounded(&bar[st ^ 1], (phase_bits >> (st ^ 1)) & 1u);
-            break;
-        }
-        if (active) {
-        const int W = d.W, H = d.H;
-        const uint32_t local = item - __ldg(tile_prefix + s);
-        const int ty = (int)(local / (uint32_t)d.tiles_x), tx = (int)(local % (uint32_t)d.tiles_x);
-        const int x0 = tx * TW, y0 = ty * TH;
-        const uint8_t *O = occ_stage(st);
-        float *tA = tau_stage(st, 0);
-        float *tB = tau_stage(st, 1);
-        const bool aco = d.model == 1;
-        const bool const_deposit = !(aco && d.deposit_mode == 1);
-
-        // Phase 0: clear the claim masks; list the agents of the tile and its
-        // 2-ring (cells outside the grid read as empty: TMA zero fill).  A
-        // warp reserves its list slots with one shared atomic.
-        for (int i = threadIdx.x; i < Lay::WIN_BYTES / 16; i += NT)
-            reinterpret_cast<uint4 *>(Cw)[i] = make_uint4(0u, 0u, 0u, 0u);
-        for (int i0 = 0; i0 < (TH + 4) * NWC; i0 += NT) {
-            const int i = i0 + threadIdx.x;
-            uint32_t found = 0;  // bit b: byte b of this word is a listed agent
-            int r = 0, wc = 0;
-            if (i < (TH + 4) * NWC) {
-                r = i / NWC;
-                wc = WC0 + i % NWC;
-                const uint32_t o4 = *reinterpret_cast<const uint32_t *>(O + (r + 1) * OW + 4 * wc);
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int cx = 4 * wc + b;
-                    if (((o4 >> (8 * b)) & 255u) && cx >= 14 && cx <= TW + 17) found |= 1u << b;
+            while (list_left) {
+                const uint32_t j = atomicAdd(&act->work, 1u);
+                if (j >= n_act) {
+                    list_left = false;
+                    break;
+                }
+                item = L_cur[j];
+                aux = (uint32_t)scenario_of(tile_prefix, n_scen, item);
+                if (live(aux)) return kItemActive;
+            }
+            for (;;) {
+                if (all_active) {
+                    const uint32_t j = atomicAdd(&act->work_nat, 1u);
+                    if (j >= total) return kItemEnd;
+                    if ((j & 31u) == 0) F_old[j >> 5] = 0u;
+                    item = j;
+                    aux = (uint32_t)scenario_of(tile_prefix, n_scen, item);
+                    if (live(aux)) return kItemActive;
+                    continue;
+                }
+                const uint32_t j0 = atomicAdd(&act->work_nat, (uint32_t)QC);
+                if (j0 >= total) return kItemEnd;
+                if ((j0 & 31u) == 0) F_old[j0 >> 5] = 0u;
+                const uint32_t fw = F_cur[j0 >> 5] >> (j0 & 31u);
+                uint32_t m = 0;
+                for (int q = 0; q < QC; ++q) {
+                    const uint32_t it = j0 + (uint32_t)q;
+                    if (it >= total || ((fw >> q) & 1u)) continue;
+                    if (live((uint32_t)scenario_of(tile_prefix, n_scen, it))) m |= 1u << q;
+                }
+                if (m) {
+                    pend_j0 = j0;
+                    pend_m = m;
+                    quiet_group(item, aux);
+                    return kItemQuiet;
                 }
             }
-            const int nf = __popc(found);
-            int incl = nf;  // inclusive warp prefix sum of nf
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
+        };
+        int st = 0;
+        uint32_t ephase = 0;
+        for (;;) {
+            uint32_t item = 0, aux = 0, kind = 0;
+            if (lane == 0) kind = claim(item, aux);
+            kind = __shfl_sync(0xffffffffu, kind, 0);
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait_bounded(&empty[st], ((ephase >> st) & 1u) ^ 1u);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            ephase ^= 1u << st;
+            if (!ok) {
+                failed = true;
+                break;
             }
-            const int warp_total = __shfl_sync(0xffffffffu, incl, 31);
-            unsigned int base = 0;
-            if (lane == 31 && warp_total) base = atomicAdd(&misc[0], (unsigned int)warp_total);
-            base = __shfl_sync(0xffffffffu, base, 31);
-            int slot = (int)base + incl - nf;
-            for (int b = 0; b < 4; ++b)
-                if (found & (1u << b)) agents[slot++] = (uint16_t)((r + 1) * OW + 4 * wc + b);
-        }
-        __syncthreads();
-
-        // Phase 1: proposals (Sec. IV.b-c), one agent per thread, from shared
-        // memory only; each proposal that targets the tile or its 1-ring
-        // sets its claim bit there.  Proposal codes are written for occupied
-        // cells only, the only cells whose codes are read.
-        {
-            const RuleParams rp{d.model, d.alpha, d.beta, d.lem_scale};
-            const int n_agents = (int)misc[0];
-            for (int a = threadIdx.x; a < n_agents; a += NT) {
-                const int oi = agents[a];
-                const int r = oi / OW - 1, cx = oi - (oi / OW) * OW;
-                const int x = x0 - 16 + cx, y = y0 - 2 + r;
-                const int g = O[oi];
-                const uint64_t cell = (uint64_t)y * (uint64_t)W + (uint64_t)x;
-                const float *tc = (g == 2 ? tB : tA) + (r + 1) * TWH + (cx - 12);
-                const int code = propose(
-                    x, y, g, W, H, cell, t, d.seed, rp,
-                    [&](int dx, int dy) { return (int)O[oi + dy * OW + dx]; }, tc, TWH);
-                Pp[r * OW + cx] = (uint8_t)code;
-                if (code) {
-                    const int tr = r - 1 + kCodeDY[code];
-                    const int tcx = cx + kCodeDX[code];
-                    if (tr >= 0 && tr < TH + 2 && tcx >= 15 && tcx <= TW + 16) {
-                        const int idx = tr * OW + tcx;
-                        atomicOr(reinterpret_cast<unsigned int *>(Cw + (idx & ~3)),
-                                 (1u << (8 - code)) << (8 * (idx & 3)));
+            if (lane == 0) {
+                item_hdr[4 * st + 0] = item;
+                item_hdr[4 * st + 1] = aux;
+                item_hdr[4 * st + 2] = kind;
+                if (kind == kItemActive) {
+                    const ScenarioDesc *d = descs + aux;
+                    const uint64_t t = d->step + (uint64_t)t_off;
+                    const int p = (int)(t & 1);
+                    const uint32_t local = item - __ldg(tile_prefix + aux);
+                    const int tiles_x = d->tiles_x;
+                    const int ty = (int)(local / (uint32_t)tiles_x), tx = (int)(local % (uint32_t)tiles_x);
+                    const bool aco = d->model == 1;
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&full[st], Lay::OH * OW + (aco ? 2 * Lay::TAU_BOX_BYTES : 0));
+                    tma_load_2d(occ_stage(st), &d->map_occ[p], tx * TW - 16, ty * TH - 3, &full[st]);
+                    if (aco) {
+                        tma_load_2d(tau_stage(st, 0), &d->map_tau[0][p], tx * TW - 4, ty * TH - 3, &full[st]);
+                        tma_load_2d(tau_stage(st, 1), &d->map_tau[1][p], tx * TW - 4, ty * TH - 3, &full[st]);
                     }
+                } else {
+                    mbar_arrive(&full[st]);  // quiet chunk or end: nothing to copy
                 }
             }
+            __syncwarp();
+            if (kind == kItemEnd) break;
+            st = (st + 1) % kStages;
         }
-        __syncthreads();
-
-        // Phase 1c: one winner per claimed cell of the tile and its 1-ring
-        // (Sec. IV.d): the only claimant, or claimant floor(r * k / 2^32) in
-        // scan order from Philox stream 2 at the target cell.  Tile cells
-        // that receive an agent go to the move list.
-        for (int i0 = 0; i0 < (TH + 2) * NWC; i0 += NT) {
-            const int i = i0 + threadIdx.x;
-            uint32_t into = 0;  // bit b: byte b is a tile cell receiving an agent
-            int r = 0, wc = 0;
-            if (i < (TH + 2) * NWC) {
-                r = i / NWC;
-                wc = WC0 + i % NWC;
-                uint32_t *cp = reinterpret_cast<uint32_t *>(Cw + r * OW + 4 * wc);
-                const uint32_t m4 = *cp;
-                if (m4) {
-                    uint32_t w4 = 0;
-                    for (int b = 0; b < 4; ++b) {
-                        const uint32_t m = (m4 >> (8 * b)) & 255u;
-                        if (!m) continue;
-                        const uint32_t k = (uint32_t)__popc(m);
-                        const int cx = 4 * wc + b;
-                        uint32_t j;
-                        if (k == 1) {
-                            j = (uint32_t)(__ffs(m) - 1);
-                        } else {
-                            const int x = x0 - 16 + cx, y = y0 - 1 + r;
-                            j = pick_claimant(m, k, (uint64_t)y * (uint64_t)W + (uint64_t)x, t, d.seed);
-                        }
-                        w4 |= ((j + 1u) | (k >= 2 ? 0x10u : 0u)) << (8 * b);
-                        if (r >= 1 && r <= TH && cx >= 16 && cx < TW + 16) into |= 1u << b;
-                    }
-                    *cp = w4;
-                }
-            }
-            const int nf = __popc(into);
-            int incl = nf;
+    } else {
+        // ------------------------------ consumers -----------------------------
+        Counts cnt;
+        int st = 0;
+        uint32_t fphase = 0;
+        for (;;) {
+            if (threadIdx.x == 0) {
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
+                for (int i = 0; i < 5; ++i) misc[i] = 0;
             }
-            const int warp_total = __shfl_sync(0xffffffffu, incl, 31);
-            unsigned int base = 0;
-            if (lane == 31 && warp_total) base = atomicAdd(&misc[1], (unsigned int)warp_total);
-            base = __shfl_sync(0xffffffffu, base, 31);
-            int slot = (int)base + incl - nf;
-            for (int b = 0; b < 4; ++b)
-                if (into & (1u << b)) moves[slot++] = (uint16_t)((r - 1) * TW + 4 * wc + b - 16);
-        }
-        __syncthreads();
-
-        // Phase 2a: per-agent bookkeeping of the moves into tile cells (ids,
-        // tour length, arrival), one move per thread.  With a constant
-        // deposit nothing below depends on it, so the dense pass starts at
-        // once and hides these global round trips; with Eq. 5 the deposits
-        // go to shared memory first.
-        {
-            const int n_moves = (int)misc[1];
-            for (int mi = threadIdx.x; mi < n_moves; mi += NT) {
-                const int li = moves[mi];
-                const int iy = li / TW, ix = li - iy * TW;
-                const int x = x0 + ix, y = y0 + iy;
-                const int w = Cw[(iy + 1) * OW + ix + 16];
-                const int j = (w & 15) - 1;
-                const int dx = kCodeDX[j + 1], dy = kCodeDY[j + 1];
-                const int inc = O[(iy + 3 + dy) * OW + ix + 16 + dx];
-                const uint64_t cell = (uint64_t)y * (uint64_t)W + (uint64_t)x;
-                const uint64_t rv = apply_move(d, cell, cell + (int64_t)dy * W + dx, inc, x,
-                                               dx != 0 && dy != 0, t);
-                ++cnt.moved;
-                cnt.conflicts += (w >> 4) & 1;
-                const unsigned crossed = (unsigned)(rv >> 32);
-                if (inc == 1) cnt.crossed_a += crossed; else cnt.crossed_b += crossed;
-                if (!const_deposit) depv[li] = __uint_as_float((uint32_t)rv);
+            bool ok = true;
+            if (threadIdx.x == 0) ok = mbar_wait_bounded(&full[st], (fphase >> st) & 1u);
+            ok = consumer_sync_and(ok);
+            fphase ^= 1u << st;
+            if (!ok) {
+                failed = true;
+                break;
             }
-        }
-        if (!const_deposit) __syncthreads();
+            const uint32_t item = item_hdr[4 * st + 0];
+            const uint32_t aux = item_hdr[4 * st + 1];
+            const uint32_t kind = item_hdr[4 * st + 2];
+            if (kind == kItemEnd) break;
 
-        // Phase 2b: per group of 4 tile cells: the winner's group enters each
-        // empty cell, cells whose agent won are vacated, pheromone evaporates
-        // (Eq. 3) and the deposit lands in the mover's own plane (Eq. 4).
-        {
-            const int p = (int)(t & 1);
-            const float q = d.q;
-            const float dep0 = d.deposit;
-            uint8_t *occ_dst = d.occ[p ^ 1];
-            float *tA_dst = d.tau[0][p ^ 1];
-            float *tB_dst = d.tau[1][p ^ 1];
-            for (int gi = threadIdx.x; gi < TH * GW; gi += NT) {
-                const int iy = gi / GW, gx = gi - iy * GW;
-                const int x = x0 + 4 * gx, y = y0 + iy;
-                if (x >= W || y >= H) continue;
-                const int cxo = 16 + 4 * gx;
-                const uint32_t o4 = *reinterpret_cast<const uint32_t *>(O + (iy + 3) * OW + cxo);
-                const uint32_t w4 = *reinterpret_cast<const uint32_t *>(Cw + (iy + 1) * OW + cxo);
-                const uint64_t cell0 = (uint64_t)y * (uint64_t)W + (uint64_t)x;
-                float va[4], vb[4];
+            if (kind == kItemQuiet) {
+                // No agent within reach: the occupancy stays empty and the
+                // pheromone evaporates (Eq. 3).  The stage holds nothing for
+                // this item: release it at once.
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[st]);
+                const ScenarioDesc &d = descs[aux >> 8];
+                const uint32_t m = aux & 255u;
+                const uint32_t first = item - __ldg(tile_prefix + (aux >> 8));
+                const int W = d.W, H = d.H, tiles_x = d.tiles_x;
+                const int p = (int)((d.step + (uint64_t)t_off) & 1);
+                const bool aco = d.model == 1;
+                // cell index of group k of tile q of the chunk, or -1
+                auto cell_of = [&](int q, int k) -> int64_t {
+                    const int gi = threadIdx.x + k * NT;
+                    if (!((m >> q) & 1u) || gi >= TH * GW) return -1;
+                    const uint32_t local = first + (uint32_t)q;
+                    const int ty = (int)(local / (uint32_t)tiles_x), tx = (int)(local % (uint32_t)tiles_x);
+                    const int iy = gi / GW, gx = gi - iy * GW;
+                    const int x = tx * TW + 4 * gx, y = ty * TH + iy;
+                    if (x >= W || y >= H) return -1;
+                    return (int64_t)y * W + x;
+                };
                 if (aco) {
-                    const int ti = (iy + 3) * TWH + 4 * gx + 4;
-                    const float4 a4 = *reinterpret_cast<const float4 *>(tA + ti);
-                    const float4 b4 = *reinterpret_cast<const float4 *>(tB + ti);
-                    va[0] = __fmul_rn(a4.x, q); va[1] = __fmul_rn(a4.y, q);
-                    va[2] = __fmul_rn(a4.z, q); va[3] = __fmul_rn(a4.w, q);
-                    vb[0] = __fmul_rn(b4.x, q); vb[1] = __fmul_rn(b4.y, q);
-                    vb[2] = __fmul_rn(b4.z, q); vb[3] = __fmul_rn(b4.w, q);
+                    float4 va[QC][QG], vb[QC][QG];
+                    const float *sA = d.tau[0][p], *sB = d.tau[1][p];
+                    // every pheromone load of the chunk first ...
+#pragma unroll
+                    for (int q = 0; q < QC; ++q)
+#pragma unroll
+                        for (int k = 0; k < QG; ++k) {
+                            const int64_t c = cell_of(q, k);
+                            if (c < 0) continue;
+                            va[q][k] = __ldcs(reinterpret_cast<const float4 *>(sA + c));
+                            vb[q][k] = __ldcs(reinterpret_cast<const float4 *>(sB + c));
+                        }
+                    // ... then the evaporated values out
+                    const float qf = d.q;
+                    float *dA = d.tau[0][p ^ 1], *dB = d.tau[1][p ^ 1];
+#pragma unroll
+                    for (int q = 0; q < QC; ++q)
+#pragma unroll
+                        for (int k = 0; k < QG; ++k) {
+                            const int64_t c = cell_of(q, k);
+                            if (c < 0) continue;
+                            const float4 a4 = va[q][k], b4 = vb[q][k];
+                            __stcs(reinterpret_cast<float4 *>(dA + c),
+                                   make_float4(__fmul_rn(a4.x, qf), __fmul_rn(a4.y, qf),
+                                               __fmul_rn(a4.z, qf), __fmul_rn(a4.w, qf)));
+                            __stcs(reinterpret_cast<float4 *>(dB + c),
+                                   make_float4(__fmul_rn(b4.x, qf), __fmul_rn(b4.y, qf),
+                                               __fmul_rn(b4.z, qf), __fmul_rn(b4.w, qf)));
+                        }
                 }
-                uint32_t n4 = o4;
-                if (o4 | w4) {
-                    const uint32_t p4 = *reinterpret_cast<const uint32_t *>(Pp + (iy + 2) * OW + cxo);
-                    n4 = 0;
+                uint8_t *occ_dst = d.occ[p ^ 1];
+#pragma unroll
+                for (int q = 0; q < QC; ++q)
+#pragma unroll
+                    for (int k = 0; k < QG; ++k) {
+                        const int64_t c = cell_of(q, k);
+                        if (c >= 0) *reinterpret_cast<uint32_t *>(occ_dst + c) = 0u;
+                    }
+                st = (st + 1) % kStages;
+                continue;
+            }
+
+            const uint32_t sc = aux;
+            const ScenarioDesc &d = descs[sc];
+            const uint64_t t = d.step + (uint64_t)t_off;
+            const int W = d.W, H = d.H;
+            const uint32_t local = item - __ldg(tile_prefix + sc);
+            const int tiles_x = d.tiles_x;
+            const int ty = (int)(local / (uint32_t)tiles_x), tx = (int)(local % (uint32_t)tiles_x);
+            const int x0 = tx * TW, y0 = ty * TH;
+            const int p = (int)(t & 1);
+            const bool aco = d.model == 1;
+            const float *tA = tau_stage(st, 0);
+            const float *tB = tau_stage(st, 1);
+            const uint8_t *O = occ_stage(st);
+            const bool const_deposit = !(aco && d.deposit_mode == 1);
+
+            // Phase 0: clear the claim masks; list the agents of the tile and its
+            // 2-ring (cells outside the grid read as empty: TMA zero fill).  A
+            // warp reserves its list slots with one shared atomic.
+            for (int i = threadIdx.x; i < Lay::WIN_BYTES / 16; i += NT)
+                reinterpret_cast<uint4 *>(Cw)[i] = make_uint4(0u, 0u, 0u, 0u);
+            for (int i0 = 0; i0 < (TH + 4) * NWC; i0 += NT) {
+                const int i = i0 + threadIdx.x;
+                uint32_t found = 0;  // bit b: byte b of this word is a listed agent
+                int r = 0, wc = 0;
+                if (i < (TH + 4) * NWC) {
+                    r = i / NWC;
+                    wc = WC0 + i % NWC;
+                    const uint32_t o4 = *reinterpret_cast<const uint32_t *>(O + (r + 1) * OW + 4 * wc);
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
-                        const int o = (o4 >> (8 * b)) & 255u;
-                        int no = o;
-                        if (o == 0) {
-                            const int w = (w4 >> (8 * b)) & 255u;
-                            if (w) {
-                                const int j = (w & 15) - 1;
-                                no = O[(iy + 3 + kCodeDY[j + 1]) * OW + cxo + b + kCodeDX[j + 1]];
-                                if (aco) {
-                                    const float dep = const_deposit ? dep0 : depv[iy * TW + 4 * gx + b];
-                                    if (no == 1) va[b] = __fadd_rn(va[b], dep);
-                                    else vb[b] = __fadd_rn(vb[b], dep);
+                        const int cx = 4 * wc + b;
+                        if (((o4 >> (8 * b)) & 255u) && cx >= 14 && cx <= TW + 17) found |= 1u << b;
+                    }
+                }
+                int slot = warp_reserve(&misc[0], __popc(found));
+                for (int b = 0; b < 4; ++b)
+                    if (found & (1u << b)) agents[slot++] = (uint16_t)((r + 1) * OW + 4 * wc + b);
+            }
+            consumer_sync();
+
+            // Phase 1 (Sec. IV.b-c), from shared memory only.  1a: forward
+            // first for every listed agent; the blocked ones are listed.  1b:
+            // the full rule for the blocked agents, one per thread, so the
+            // random draws run with full warps.  Each proposal that targets
+            // the tile or its 1-ring sets its claim bit there.  Proposal codes
+            // are written for occupied cells only, the only cells whose codes
+            // are read.
+            auto claim_target = [&](int r, int cx, int code) {
+                const int tr = r - 1 + kCodeDY[code];
+                const int tcx = cx + kCodeDX[code];
+                if (tr >= 0 && tr < TH + 2 && tcx >= 15 && tcx <= TW + 16) {
+                    const int idx = tr * OW + tcx;
+                    atomicOr(reinterpret_cast<unsigned int *>(Cw + (idx & ~3)),
+                             (1u << (8 - code)) << (8 * (idx & 3)));
+                }
+            };
+            {
+                const int n_agents = (int)misc[0];
+                for (int a0 = 0; a0 < n_agents; a0 += NT) {
+                    const int a = a0 + threadIdx.x;
+                    bool is_blocked = false;
+                    int oi = 0;
+                    if (a < n_agents) {
+                        oi = agents[a];
+                        const int r = oi / OW - 1, cx = oi - (oi / OW) * OW;
+                        const int x = x0 - 16 + cx, y = y0 - 2 + r;
+                        const int g = O[oi];
+                        const int code = forward_first(x, y, g, W, H,
+                                                       [&](int dx, int dy) { return (int)O[oi + dy * OW + dx]; });
+                        if (code < 0) {
+                            is_blocked = true;
+                        } else {
+                            Pp[r * OW + cx] = (uint8_t)code;
+                            if (code) claim_target(r, cx, code);
+                        }
+                    }
+                    const int slot = warp_reserve(&misc[2], is_blocked ? 1 : 0);
+                    if (is_blocked) blocked[slot] = (uint16_t)oi;
+                }
+            }
+            consumer_sync();
+            {
+                const RuleParams rp{d.model, d.alpha, d.beta, d.lem_scale};
+                const int n_blocked = (int)misc[2];
+                for (int a = threadIdx.x; a < n_blocked; a += NT) {
+                    const int oi = blocked[a];
+                    const int r = oi / OW - 1, cx = oi - (oi / OW) * OW;
+                    const int x = x0 - 16 + cx, y = y0 - 2 + r;
+                    const int g = O[oi];
+                    const uint64_t cell = (uint64_t)y * (uint64_t)W + (uint64_t)x;
+                    const float *tc = (g == 2 ? tB : tA) + (r + 1) * TWH + (cx - 12);
+                    const int code = propose(
+                        x, y, g, W, H, cell, t, d.seed, rp,
+                        [&](int dx, int dy) { return (int)O[oi + dy * OW + dx]; }, tc, TWH);
+                    Pp[r * OW + cx] = (uint8_t)code;
+                    if (code) claim_target(r, cx, code);
+                }
+            }
+            consumer_sync();
+
+            // Phase 1c: one winner per claimed cell of the tile and its 1-ring
+            // (Sec. IV.d).  A single claimant wins at once; cells with k >= 2
+            // claimants are listed and draw claimant floor(r * k / 2^32) in scan
+            // order from Philox stream 2 at the target cell, one cell per
+            // thread.  Tile cells that receive an agent go to the move list.
+            for (int i0 = 0; i0 < (TH + 2) * NWC; i0 += NT) {
+                const int i = i0 + threadIdx.x;
+                uint32_t into = 0;   // bit b: byte b is a tile cell receiving an agent
+                uint32_t multi = 0;  // bit b: byte b has two or more claimants
+                int r = 0, wc = 0;
+                if (i < (TH + 2) * NWC) {
+                    r = i / NWC;
+                    wc = WC0 + i % NWC;
+                    uint32_t *cp = reinterpret_cast<uint32_t *>(Cw + r * OW + 4 * wc);
+                    const uint32_t m4 = *cp;
+                    if (m4) {
+                        uint32_t w4 = 0;
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const uint32_t m = (m4 >> (8 * b)) & 255u;
+                            if (!m) continue;
+                            const int cx = 4 * wc + b;
+                            if (m & (m - 1u)) {
+                                multi |= 1u << b;
+                                w4 |= m << (8 * b);  // resolved below
+                            } else {
+                                w4 |= (uint32_t)__ffs(m) << (8 * b);
+                            }
+                            if (r >= 1 && r <= TH && cx >= 16 && cx < TW + 16) into |= 1u << b;
+                        }
+                        *cp = w4;
+                    }
+                }
+                int slot = warp_reserve(&misc[1], __popc(into));
+                for (int b = 0; b < 4; ++b)
+                    if (into & (1u << b)) moves[slot++] = (uint16_t)((r - 1) * TW + 4 * wc + b - 16);
+                slot = warp_reserve(&misc[3], __popc(multi));
+                for (int b = 0; b < 4; ++b)
+                    if (multi & (1u << b)) conflicts[slot++] = (uint16_t)(r * OW + 4 * wc + b);
+            }
+            consumer_sync();
+            {
+                const int n_conf = (int)misc[3];
+                for (int ci = threadIdx.x; ci < n_conf; ci += NT) {
+                    const int idx = conflicts[ci];
+                    const int r = idx / OW, cx = idx - r * OW;
+                    const uint32_t m = Cw[idx];
+                    const uint32_t k = (uint32_t)__popc(m);
+                    const int x = x0 - 16 + cx, y = y0 - 1 + r;
+                    const uint32_t j =
+                        pick_claimant(m, k, (uint64_t)y * (uint64_t)W + (uint64_t)x, t, d.seed);
+                    Cw[idx] = (uint8_t)((j + 1u) | 0x10u);
+                }
+            }
+            consumer_sync();
+
+            // Phase 2a: per-agent bookkeeping of the moves into tile cells (ids,
+            // tour length, arrival), one move per thread.  Within a step a cell
+            // that is read as a source (occupied at t) is never written as a
+            // target (empty at t), so the id loads may take the non-coherent
+            // path and all of them are in flight together.  With a constant
+            // deposit nothing below depends on this pass; with Eq. 5 the
+            // deposits go to shared memory first.
+            {
+                const int n_moves = (int)misc[1];
+                for (int mi = threadIdx.x; mi < n_moves; mi += NT) {
+                    const int li = moves[mi];
+                    const int iy = li / TW, ix = li - iy * TW;
+                    const int x = x0 + ix, y = y0 + iy;
+                    const int w = Cw[(iy + 1) * OW + ix + 16];
+                    const int j = (w & 15) - 1;
+                    const int dx = kCodeDX[j + 1], dy = kCodeDY[j + 1];
+                    const int inc = O[(iy + 3 + dy) * OW + ix + 16 + dx];
+                    const uint64_t cell = (uint64_t)y * (uint64_t)W + (uint64_t)x;
+                    const uint32_t id = __ldg(d.ids + cell + (int64_t)dy * W + dx);
+                    const uint64_t rv = apply_move_id(d, cell, id, inc, x, dx != 0 && dy != 0, t);
+                    ++cnt.moved;
+                    cnt.conflicts += (w >> 4) & 1;
+                    const unsigned crossed = (unsigned)(rv >> 32);
+                    if (inc == 1) cnt.crossed_a += crossed; else cnt.crossed_b += crossed;
+                    if (!const_deposit) depv[li] = __uint_as_float((uint32_t)rv);
+                }
+            }
+            if (!const_deposit) consumer_sync();
+
+            // Phase 2b: per group of 4 tile cells: the winner's group enters each
+            // empty cell, cells whose agent won are vacated, pheromone evaporates
+            // (Eq. 3) and the deposit lands in the mover's own plane (Eq. 4).
+            // Agents at t+1 on the tile's border mark the neighbouring tiles
+            // they touch: bit (dy + 1) * 3 + (dx + 1) for tile (tx + dx, ty + dy).
+            uint32_t mark = 0;
+            {
+                const float q = d.q;
+                const float dep0 = d.deposit;
+                uint8_t *occ_dst = d.occ[p ^ 1];
+                float *tA_dst = d.tau[0][p ^ 1];
+                float *tB_dst = d.tau[1][p ^ 1];
+                for (int gi = threadIdx.x; gi < TH * GW; gi += NT) {
+                    const int iy = gi / GW, gx = gi - iy * GW;
+                    const int x = x0 + 4 * gx, y = y0 + iy;
+                    if (x >= W || y >= H) continue;
+                    const int cxo = 16 + 4 * gx;
+                    const uint32_t o4 = *reinterpret_cast<const uint32_t *>(O + (iy + 3) * OW + cxo);
+                    const uint32_t w4 = *reinterpret_cast<const uint32_t *>(Cw + (iy + 1) * OW + cxo);
+                    const uint64_t cell0 = (uint64_t)y * (uint64_t)W + (uint64_t)x;
+                    float va[4], vb[4];
+                    if (aco) {
+                        const int ti = (iy + 3) * TWH + 4 * gx + 4;
+                        const float4 a4 = *reinterpret_cast<const float4 *>(tA + ti);
+                        const float4 b4 = *reinterpret_cast<const float4 *>(tB + ti);
+                        va[0] = __fmul_rn(a4.x, q); va[1] = __fmul_rn(a4.y, q);
+                        va[2] = __fmul_rn(a4.z, q); va[3] = __fmul_rn(a4.w, q);
+                        vb[0] = __fmul_rn(b4.x, q); vb[1] = __fmul_rn(b4.y, q);
+                        vb[2] = __fmul_rn(b4.z, q); vb[3] = __fmul_rn(b4.w, q);
+                    }
+                    uint32_t n4 = o4;
+                    if (o4 | w4) {
+                        const uint32_t p4 = *reinterpret_cast<const uint32_t *>(Pp + (iy + 2) * OW + cxo);
+                        n4 = 0;
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const int o = (o4 >> (8 * b)) & 255u;
+                            int no = o;
+                            if (o == 0) {
+                                const int w = (w4 >> (8 * b)) & 255u;
+                                if (w) {
+                                    const int j = (w & 15) - 1;
+                                    no = O[(iy + 3 + kCodeDY[j + 1]) * OW + cxo + b + kCodeDX[j + 1]];
+                                    if (aco) {
+                                        const float dep = const_deposit ? dep0 : depv[iy * TW + 4 * gx + b];
+                                        if (no == 1) va[b] = __fadd_rn(va[b], dep);
+                                        else vb[b] = __fadd_rn(vb[b], dep);
+                                    }
+                                }
+                            } else {
+                                const int code = (p4 >> (8 * b)) & 255u;
+                                if (code) {
+                                    const int wt = Cw[(iy + 1 + kCodeDY[code]) * OW + cxo + b + kCodeDX[code]];
+                                    if ((wt & 15) == 9 - code) no = 0;  // this agent won its target
                                 }
                             }
-                        } else {
-                            const int code = (p4 >> (8 * b)) & 255u;
-                            if (code) {
-                                const int wt = Cw[(iy + 1 + kCodeDY[code]) * OW + cxo + b + kCodeDX[code]];
-                                if ((wt & 15) == 9 - code) no = 0;  // this agent won its target
-                            }
+                            n4 |= (uint32_t)no << (8 * b);
                         }
-                        n4 |= (uint32_t)no << (8 * b);
+                    }
+                    if (n4) {
+                        const bool top = iy == 0, bottom = iy == TH - 1;
+                        uint32_t mk = 1u << 4;
+                        if (top) mk |= 1u << 1;
+                        if (bottom) mk |= 1u << 7;
+                        if (gx == 0 && (n4 & 255u)) {
+                            mk |= 1u << 3;
+                            if (top) mk |= 1u << 0;
+                            if (bottom) mk |= 1u << 6;
+                        }
+                        if (gx == GW - 1 && (n4 >> 24)) {
+                            mk |= 1u << 5;
+                            if (top) mk |= 1u << 2;
+                            if (bottom) mk |= 1u << 8;
+                        }
+                        mark |= mk;
+                    }
+                    *reinterpret_cast<uint32_t *>(occ_dst + cell0) = n4;
+                    if (aco) {
+                        *reinterpret_cast<float4 *>(tA_dst + cell0) = make_float4(va[0], va[1], va[2], va[3]);
+                        *reinterpret_cast<float4 *>(tB_dst + cell0) = make_float4(vb[0], vb[1], vb[2], vb[3]);
                     }
                 }
-                *reinterpret_cast<uint32_t *>(occ_dst + cell0) = n4;
-                if (aco) {
-                    *reinterpret_cast<float4 *>(tA_dst + cell0) = make_float4(va[0], va[1], va[2], va[3]);
-                    *reinterpret_cast<float4 *>(tB_dst + cell0) = make_float4(vb[0], vb[1], vb[2], vb[3]);
+            }
+            mark = __reduce_or_sync(0xffffffffu, mark);
+            if (lane == 0 && mark) atomicOr(&misc[4], mark);
+            // Every consumer is done with the stage and the work area.
+            consumer_sync();
+            if (lane == 0) mbar_arrive(&empty[st]);
+            mark = misc[4];
+
+            // Marks for the next step: lanes 0-8 of warp 0 set the flags of the
+            // marked tiles; the tiles whose flag they set first join the next
+            // step's list.
+            if (mark && warp == 0) {
+                const int tiles_y = d.tiles_y;
+                bool mine = false;
+                uint32_t nb = 0;
+                if (lane < 9 && ((mark >> lane) & 1u)) {
+                    const int nx = tx + lane % 3 - 1, ny = ty + lane / 3 - 1;
+                    if (nx >= 0 && nx < tiles_x && ny >= 0 && ny < tiles_y) {
+                        nb = (item - local) + (uint32_t)ny * (uint32_t)tiles_x + (uint32_t)nx;
+                        const uint32_t bit = 1u << (nb & 31u);
+                        mine = (atomicOr(&F_next[nb >> 5], bit) & bit) == 0;
+                    }
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, mine);
+                if (m) {
+                    uint32_t b0 = 0;
+                    if (lane == 0) b0 = atomicAdd(n_next, (unsigned int)__popc(m));
+                    b0 = __shfl_sync(0xffffffffu, b0, 0);
+                    if (mine) L_next[b0 + (uint32_t)__popc(m & ((1u << lane) - 1u))] = nb;
                 }
             }
-        }
             flush_counts(d, cnt, local);
-        }  // active
-        // publish the index claimed above; every thread is done with this item
-        if (threadIdx.x == 0) misc[2] = next2;
-        __syncthreads();
-        item = next;
-        next = misc[2];
-        st ^= 1;
+            st = (st + 1) % kStages;
+        }
+        if (failed && threadIdx.x == 0) {
+            // give a copy still in flight for the other stage a bounded chance
+            // to land before the CTA leaves
+            const int o = (st + 1) % kStages;
+            (void)mbar_wait_bounded(&full[o], (fphase >> o) & 1u);
+        }
     }
-    finish_launch(ctr);
+    // A wait that gave up is reported to every scenario of the work list.
+    if (failed && (threadIdx.x == 0 || threadIdx.x == kFusedConsumers))
+        for (int i = 0; i < n_scen; ++i) atomicExch(descs[i].error, kErrTimeout);
+
+    // The last CTA to finish re-arms the work counters and rotates the
+    // activity generations for the next launch.
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int ticket = atomicAdd(&act->ticket, 1u);
+        if (ticket == gridDim.x - 1) {
+            act->work = 0u;
+            act->work_nat = 0u;
+            act->n_act[(ph + 2u) % 3u] = 0u;
+            act->reset = 0u;
+            act->phase = (ph + 1u) % 3u;
+            act->ticket = 0u;
+            __threadfence();
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -792,40 +1023,6 @@ __device__ __forceinline__ bool cta_wait_tma(uint64_t *bar, uint32_t parity)
     bool ok = true;
     if (threadIdx.x == 0) ok = mbar_wait_bounded(bar, parity);
     return __syncthreads_and(ok);
-}
-
-// Appends `n` entries of this thread to a shared list with one shared atomic
-// per warp; returns the first slot of this thread.  All 32 lanes must call.
-__device__ __forceinline__ int warp_reserve(unsigned int *counter, int n)
-{
-    const int lane = threadIdx.x & 31;
-    int incl = n;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    unsigned int base = 0;
-    if (lane == 31 && total) base = atomicAdd(counter, (unsigned int)total);
-    base = __shfl_sync(0xffffffffu, base, 31);
-    return (int)base + incl - n;
-}
-
-// Forward-first part of a proposal (Sec. III): 0 for an agent on its goal
-// column, the forward code when the forward cell is in the grid and empty,
-// -1 when the agent is blocked and needs the full rule.
-template <class OccFn>
-__device__ __forceinline__ int forward_first(int x, int y, int g, int W, int H, OccFn occ)
-{
-    if ((g == 1 && x == W - 1) || (g == 2 && x == 0)) return 0;
-    const int code = kFrameCode[g - 1][1];
-    const int dx = kCodeDX[code];
-    const int nx = x + dx;
-    if ((unsigned)nx < (unsigned)W && occ(dx, 0) == 0) return code;
-    (void)y;
-    (void)H;
-    return -1;
 }
 
 // Copies a scenario's descriptor header into shared memory (16 bytes per
@@ -1360,13 +1557,13 @@ static cudaError_t ensure_fused_attr()
 
 template <int TW, int TH>
 static cudaError_t launch_fused_t(const ScenarioDesc *d_descs, const uint32_t *d_prefix, int n,
-                                  uint32_t total, int t_off, unsigned int *done, int grid,
+                                  uint32_t total, int t_off, ActivityCtl *act, int grid,
                                   cudaStream_t stream)
 {
     cudaError_t e = ensure_fused_attr<TW, TH>();
     if (e != cudaSuccess) return e;
     fused_step_kernel<TW, TH><<<grid, kFusedThreads, FusedLayout<TW, TH>::SMEM, stream>>>(
-        d_descs, d_prefix, n, total, t_off, done);
+        d_descs, d_prefix, n, total, t_off, act);
     return cudaGetLastError();
 }
 
@@ -1393,11 +1590,11 @@ bool tile_supported(int tile_w, int tile_h)
 
 cudaError_t launch_fused_step(const ScenarioDesc *d_descs, const uint32_t *d_tile_prefix, int n,
                               uint32_t total_tiles, int t_off, int tile_w, int tile_h, int grid,
-                              unsigned int *done, cudaStream_t stream)
+                              ActivityCtl *act, cudaStream_t stream)
 {
 #define PEDSIM_TILE_LAUNCH(w, h)                                                               \
     if (tile_w == w && tile_h == h)                                                            \
-        return launch_fused_t<w, h>(d_descs, d_tile_prefix, n, total_tiles, t_off, done, grid,  \
+        return launch_fused_t<w, h>(d_descs, d_tile_prefix, n, total_tiles, t_off, act, grid,   \
                                     stream);
     PEDSIM_TILES(PEDSIM_TILE_LAUNCH)
 #undef PEDSIM_TILE_LAUNCH
@@ -1413,25 +1610,6 @@ int fused_blocks_per_sm(int tile_w, int tile_h)
 }
 
 int fused_threads() { return kFusedThreads; }
-
-// Launch that may overlap the previous kernel in the stream (programmatic
-// dependent launch); the kernel orders itself with pdl_wait.
-template <class... KArgs, class... Args>
-static cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block,
-                              cudaStream_t stream, Args... args)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
-}
 
 bool pipeline_tile_supported(int tile_w, int tile_h)
 {

@@ -25,7 +25,7 @@ _lib = C.CDLL(LIB_PATH)
 
 OK, EINVAL, ENOMEM, ENOSPC, ECUDA, ETIMEDOUT, ENOENT = 0, -22, -12, -28, -5, -110, -2
 LEM, ACO = 0, 1
-VARIANT_TILED, VARIANT_TWO_PASS, VARIANT_FUSED = 0, 1, 2
+VARIANT_TILED, VARIANT_TWO_PASS, VARIANT_FUSED, VARIANT_AGENT = 0, 1, 2, 3
 
 
 class SimParams(C.Structure):

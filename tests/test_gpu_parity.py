@@ -1,8 +1,9 @@
 """GPU parity: the CUDA path through the C ABI equals the CPU oracle bit for
 bit (tolerance 0: occupancy, ids, both pheromone planes as raw bits,
 per-agent arrival and tour arrays, counters), at every step on small grids,
-on the single-scenario workloads at full size, for every tile shape and both
-step variants, on edge cases, after checkpoint/resume, and for batched runs.
+on the single-scenario workloads at full size, for every tile shape and
+every step variant, on edge cases, after checkpoint/resume, and for batched
+runs.
 """
 import numpy as np
 import pytest
@@ -17,6 +18,11 @@ if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 from paper_1412_4933_gb300 import pedsim as P  # noqa: E402
+
+# Step variants that keep their own state between steps (the two-pass
+# variant is the plain baseline and runs on the small grids only).
+VARIANTS = [P.VARIANT_TILED, P.VARIANT_FUSED, P.VARIANT_AGENT]
+VARIANT_IDS = ["tiled", "fused", "agent"]
 
 
 def oparams(sc):
@@ -37,9 +43,12 @@ def assert_same(sim, orc, label, aco=True, agents=True):
         assert np.array_equal(a["tour"].view(np.uint32), o["tour"].view(np.uint32)), f"{label}: tour"
 
 
-def make_pair(sc, variant=P.VARIANT_TILED, tiling=None):
+def make_pair(sc, variant=None, tiling=None):
+    """The CUDA path (the library's default variant unless one is given)
+    and the oracle, both placed with the scenario's seed."""
     sim = P.Sim(sc.W, sc.H, P.params_of(sc))
-    sim.set_variant(variant)
+    if variant is not None:
+        sim.set_variant(variant)
     if tiling:
         sim.set_tiling(*tiling)
     sim.place(sc.seed)
@@ -62,8 +71,8 @@ def test_placement_matches_oracle(sc):
     assert sim.stats() == orc.stats()
 
 
-@pytest.mark.parametrize("variant", [P.VARIANT_TILED, P.VARIANT_TWO_PASS, P.VARIANT_FUSED],
-                         ids=["tiled", "two_pass", "fused"])
+@pytest.mark.parametrize("variant", VARIANTS + [P.VARIANT_TWO_PASS],
+                         ids=VARIANT_IDS + ["two_pass"])
 @pytest.mark.parametrize("sc", SMALL, ids=lambda s: s.name)
 def test_every_step_small(sc, variant):
     sim, orc = make_pair(sc, variant)
@@ -98,10 +107,11 @@ def test_every_tile_shape(tiling):
     assert sim.stats() == orc.stats()
 
 
+@pytest.mark.parametrize("variant", VARIANTS, ids=VARIANT_IDS)
 @pytest.mark.parametrize("sc", [WL.LEM_256, WL.ACO_512], ids=lambda s: s.name)
-def test_workload_every_step(sc):
+def test_workload_every_step(sc, variant):
     """Full step count; every step for the first 64, then every 16 (graph)."""
-    sim, orc = make_pair(sc)
+    sim, orc = make_pair(sc, variant)
     aco = sc.model == WL.ACO
     t = 0
     while t < sc.steps:
@@ -118,7 +128,8 @@ def test_workload_every_step(sc):
 
 def test_aco_2048_full_run():
     """The 100K-agent ACO workload at full size for its full 2000 steps, in
-    the launch configuration the benchmark times (fused, graph replays)."""
+    the launch configuration the benchmark times (the library's default
+    variant, graph replays)."""
     sc = WL.ACO_2048
     sim, orc = make_pair(sc)
     done = 0
@@ -145,9 +156,10 @@ EDGE = [
 ]
 
 
+@pytest.mark.parametrize("variant", VARIANTS, ids=VARIANT_IDS)
 @pytest.mark.parametrize("sc", EDGE, ids=lambda s: s.name)
-def test_edge_cases(sc):
-    sim, orc = make_pair(sc)
+def test_edge_cases(sc, variant):
+    sim, orc = make_pair(sc, variant)
     aco = sc.model == WL.ACO
     for t in range(sc.steps):
         sim.step(1)
@@ -156,8 +168,9 @@ def test_edge_cases(sc):
     assert sim.stats() == orc.stats()
 
 
+@pytest.mark.parametrize("variant", VARIANTS, ids=VARIANT_IDS)
 @pytest.mark.parametrize("model", [WL.LEM, WL.ACO])
-def test_random_dense_states_one_step(model):
+def test_random_dense_states_one_step(model, variant):
     """Arbitrary dense states (including wall contact) loaded through
     sim_set_state; one step from each equals the oracle's."""
     rng = np.random.default_rng(17 + model)
@@ -179,6 +192,7 @@ def test_random_dense_states_one_step(model):
         step = int(rng.integers(0, 1000))
         seed = int(rng.integers(0, 2**63))
         sim = P.Sim(W, H, P.make_params(n_per_side=n // 2, **prm))
+        sim.set_variant(variant)
         sim.set_state(seed, step, occ, ids, tauA, tauB, arrival)
         orc = O.Oracle(W, H, O.make_params(n_per_side=n // 2, **prm), seed,
                        state={"occ": occ, "ids": ids, "tauA": tauA, "tauB": tauB,
@@ -190,13 +204,15 @@ def test_random_dense_states_one_step(model):
             assert_same(sim, orc, f"trial {trial} step {k + 1}", aco=model == WL.ACO)
 
 
+@pytest.mark.parametrize("variant", VARIANTS, ids=VARIANT_IDS)
 @pytest.mark.parametrize("sc", [SMALL[1], EDGE[4]], ids=lambda s: s.name)
-def test_checkpoint_resume_bit_exact(sc):
-    a, orc = make_pair(sc)
+def test_checkpoint_resume_bit_exact(sc, variant):
+    a, orc = make_pair(sc, variant)
     a.step(23)
     blob = a.save()
     a.step(41)
     b = P.Sim(sc.W, sc.H, P.params_of(sc))
+    b.set_variant(variant)
     b.load(blob)
     b.step(41)
     orc.step(64)
@@ -217,9 +233,11 @@ def test_runs_on_a_side_stream():
     assert_same(sim, orc, "side stream")
 
 
-def test_batch_matches_single_runs():
+@pytest.mark.parametrize("variant", VARIANTS, ids=VARIANT_IDS)
+def test_batch_matches_single_runs(variant):
     scs = WL.batched_scenarios(count=12, steps=40, side_lo=64, side_hi=256)
     batch = P.Batch(scs)
+    batch.set_variant(variant)
     batch.step(3)
     batch.step(37)
     for i, sc in enumerate(scs):
@@ -233,3 +251,16 @@ def test_batch_matches_single_runs():
             assert np.array_equal(g["tauB"].view(np.uint32), o["tauB"].view(np.uint32))
         assert batch.stats(i) == orc.stats()
     assert batch.device_status() == 0
+
+
+def test_variant_switch_mid_run():
+    """Switching variants between steps continues the same trajectory (the
+    agent variant rebuilds its positions from the planes)."""
+    sc = SMALL[2]
+    sim, orc = make_pair(sc, P.VARIANT_TILED)
+    for v in (P.VARIANT_AGENT, P.VARIANT_FUSED, P.VARIANT_AGENT, P.VARIANT_TILED):
+        sim.set_variant(v)
+        sim.step(13)
+        orc.step(13)
+        assert_same(sim, orc, f"after variant {v}")
+    assert sim.stats() == orc.stats()
