@@ -11,9 +11,9 @@ dirty lines happen before the step rather than inside it (the write-only
 flush is reported beside it as `flushed_write_only`).
 
 Also reported on the same line:
-  roofline      the step's kernels (propose, stream, resolve): algorithmic
-                bytes (18 B/cell) / step time vs the measured HBM copy
-                bandwidth
+  roofline      the step's kernels (proposals + stream, resolution):
+                algorithmic bytes (18 B/cell) / step time vs the measured HBM
+                copy bandwidth
   cpu_baseline  the single-threaded CPU oracle on a bounded sample
   e2e           the same metric end to end through the C ABI with host
                 buffers: H2D of the initial state (pinned), the scenario's
@@ -54,9 +54,9 @@ KERNEL_SOURCES = ["paper_1412_4933_gb300/csrc/pedsim_agent.cu",
                   "paper_1412_4933_gb300/csrc/pedsim_rules.cuh",
                   "paper_1412_4933_gb300/csrc/pedsim_ptx.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "agent_step_aco_2048x2048_traffic.md")
-# kernels of one step of the default (agent-parallel) variant: proposals,
-# stream, resolution, plus the step-index kernel after every sim_step call
-KERNELS_PER_STEP_CALL = 4
+# kernels of one step of the default (agent-parallel) variant: proposals and
+# stream in one kernel, then resolution (which also advances the step index)
+KERNELS_PER_STEP_CALL = 2
 
 
 def kernel_source_hash() -> str:
@@ -402,9 +402,9 @@ def run_gpu(args, sc):
     ms_per_step = elapsed_max * 1e3 / args.steps
 
     # roofline of the step: algorithmic bytes / time.  The per-step time holds
-    # all of the step's kernels (the streaming pass, which moves the bytes,
-    # overlaps the proposal pass; the resolution pass and the step-index
-    # kernel follow it), so this is a lower bound of the streaming pass's rate
+    # all of the step's kernels (the first kernel streams the bytes with the
+    # proposals interleaved; the resolution kernel and the step-index kernel
+    # follow it), so this is a lower bound of the streaming part's rate
     algo_bytes = ALGO_BYTES_PER_CELL[sc.model] * sc.cells
     peak, peak_kind = measured_peak()
     step_s = elapsed / args.steps
@@ -412,7 +412,7 @@ def run_gpu(args, sc):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": recorded_traffic(),
                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes,
-                "kernel": "agent_propose_kernel + stream_kernel + agent_resolve_kernel"}
+                "kernel": "agent_stage1_kernel + agent_resolve_kernel"}
 
     extra = {}
     if rank == 0 and not args.quick:

@@ -1,12 +1,13 @@
 // Agent-parallel step (PEDSIM_VARIANT_AGENT) of the pedestrian cellular
 // automaton (sm_103a).  One synchronous step (Sec. IV.b-d) is split by
-// access pattern instead of by tile:
+// access pattern instead of by tile, in two kernels:
 //
-//   agent_propose_kernel  one thread per agent: forward first, else the full
+//   agent_stage1_kernel   two CTA roles, interleaved over the grid:
+//     proposal blocks     one thread per agent: forward first, else the full
 //                         rule (Eq. 1 LEM rank draw, Eq. 2 ACO roulette) from
 //                         the occupancy and pheromone at t; the direction code
 //                         goes to the agent's cell of the proposal plane
-//   stream_kernel         every cell: occupancy copied to the plane of t+1,
+//     stream blocks       every cell: occupancy copied to the plane of t+1,
 //                         both pheromone planes evaporated (Eq. 3); a pure
 //                         16-byte-vector stream, the HBM-bound part of the step
 //   agent_resolve_kernel  one thread per agent with a proposal: the claimants
@@ -17,13 +18,13 @@
 //                         and arrival, and its deposit (Eq. 4/5) on top of the
 //                         evaporated value
 //
-// The proposal and streaming passes touch disjoint outputs and run together:
-// the three kernels are chained by programmatic dependent launch in the
-// order propose -> stream -> resolve.  The proposal pass waits for the
-// previous step and then releases the streaming pass, which therefore starts
-// on a complete state; the streaming pass waits for the proposal pass at its
-// end, so that the resolution pass, which waits for the streaming pass,
-// sees both.
+// The two roles write disjoint outputs, so the proposals run inside the
+// stream instead of before it.  The resolution kernel is chained by
+// programmatic dependent launch: the first kernel releases it as soon as all
+// of its CTAs have started, so its CTAs are resident before the first kernel
+// ends, and it waits for the first kernel's completion.  The last CTA of
+// the resolution kernel advances the step index itself, so a step is two
+// launches and a captured graph replays at any step.
 #include "pedsim_internal.h"
 #include "pedsim_rules.cuh"
 #include "pedsim_ptx.cuh"
@@ -44,23 +45,18 @@ __device__ __forceinline__ int block_scenario(const uint32_t *__restrict__ prefi
     return lo;
 }
 
-__global__ void __launch_bounds__(kAgentBlock)
-agent_propose_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__restrict__ agent_prefix,
-                     int n_scen, int t_off)
+// Proposal of agent index a (id a + 1) at step t.  The agent's code goes
+// to its per-agent byte, and its claim bit (scan offset 8 - code seen from
+// the target) is OR-ed into the target's byte of claim plane t & 1.  The
+// agent also clears, in the other plane (written next at step t + 1), the
+// byte of the target it claimed at step t - 1: that target is its cell now
+// if it moved, else its cell plus its previous direction.
+__device__ __forceinline__ void propose_agent(const ScenarioDesc &d, uint32_t a, uint64_t t)
 {
-    // The state at t is the previous step's output: wait for it, then let
-    // the streaming pass of this step start.
-    pdl_wait();
-    pdl_trigger();
-    const int s = block_scenario(agent_prefix, n_scen, blockIdx.x);
-    const ScenarioDesc &d = descs[s];
-    const uint64_t t = d.step + (uint64_t)t_off;
-    const uint32_t a = (blockIdx.x - __ldg(agent_prefix + s)) * kAgentBlock + threadIdx.x;
-    if (t >= d.end_step || a >= 2u * d.n_per_side) return;
     const uint32_t id = a + 1u;
     const int W = d.W, H = d.H;
-    // read-only cached loads: this kernel writes none of the planes it reads
     const uint32_t cell = __ldg(d.pos + id);
+    const int prev = __ldg(d.acode + id);
     const int x = (int)(cell % (uint32_t)W), y = (int)(cell / (uint32_t)W);
     const int p = (int)(t & 1);
     const uint8_t *occ = d.occ[p];
@@ -71,143 +67,242 @@ agent_propose_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__r
         x, y, g, W, H, (uint64_t)cell, t, d.seed, rp,
         [&](int dx, int dy) { return (int)__ldg(occ + ((int64_t)cell + (int64_t)dy * W + dx)); },
         tp ? tp + cell : nullptr, W);
-    // the plane serves the neighbours' claim tests, the per-agent byte the
-    // agent's own resolution
-    d.prop[cell] = (uint8_t)code;
+    const int pc = prev & 15;
+    if (pc) {
+        const int64_t old_target =
+            (prev & 0x80) ? (int64_t)cell : (int64_t)cell + (int64_t)kCodeDY[pc] * W + kCodeDX[pc];
+        d.claim[p ^ 1][old_target] = 0;
+    }
+    if (code) {
+        const int64_t target = (int64_t)cell + (int64_t)kCodeDY[code] * W + kCodeDX[code];
+        uint8_t *cb = d.claim[p] + target;
+        const uintptr_t addr = reinterpret_cast<uintptr_t>(cb);
+        atomicOr(reinterpret_cast<unsigned int *>(addr & ~(uintptr_t)3),
+                 (1u << (8 - code)) << (8 * (unsigned)(addr & 3)));
+    }
     d.acode[id] = (uint8_t)(code | (g << 4));
 }
 
-__global__ void __launch_bounds__(kStreamThreads)
-stream_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__restrict__ cell_prefix,
-              int n_scen, int t_off)
+// Occupancy copy and evaporation of cell block b (kCellBlock cells) of the
+// work list.  Reads bypass L1 (.cg): the data is streamed once.
+__device__ __forceinline__ void stream_block(const ScenarioDesc *__restrict__ descs,
+                                             const uint32_t *__restrict__ cell_prefix, int n_scen,
+                                             uint32_t b)
 {
-    // Started by the proposal pass after the previous step completed.  Reads
-    // bypass L1 (.cg), so no line cached before that point is used.
-    const int s = block_scenario(cell_prefix, n_scen, blockIdx.x);
+    const int s = block_scenario(cell_prefix, n_scen, b);
     const ScenarioDesc &d = descs[s];
-    const uint64_t t = d.step + (uint64_t)t_off;
-    if (t < d.end_step) {
-        const size_t cells = (size_t)d.W * (size_t)d.H;
-        const size_t c0 = (size_t)(blockIdx.x - __ldg(cell_prefix + s)) * kCellBlock;
-        const int p = (int)(t & 1);
-        const bool aco = d.model == 1;
-        // occupancy: 16 cells per thread; pheromone: 4 float4 per plane and
-        // thread, consecutive threads on consecutive vectors
-        const size_t co = c0 + 16 * (size_t)threadIdx.x;
-        uint4 o = make_uint4(0u, 0u, 0u, 0u);
-        if (co < cells) o = __ldcg(reinterpret_cast<const uint4 *>(d.occ[p] + co));
-        float4 va[4], vb[4];
-        if (aco) {
+    const uint64_t t = d.step;
+    if (t >= d.end_step) return;
+    const size_t cells = (size_t)d.W * (size_t)d.H;
+    const size_t c0 = (size_t)(b - __ldg(cell_prefix + s)) * kCellBlock;
+    const int p = (int)(t & 1);
+    const bool aco = d.model == 1;
+    // occupancy: 16 cells per thread; pheromone: 4 float4 per plane and
+    // thread, consecutive threads on consecutive vectors
+    const size_t co = c0 + 16 * (size_t)threadIdx.x;
+    uint4 o = make_uint4(0u, 0u, 0u, 0u);
+    if (co < cells) o = __ldcg(reinterpret_cast<const uint4 *>(d.occ[p] + co));
+    float4 va[4], vb[4];
+    if (aco) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const size_t c = c0 + 4 * ((size_t)k * kStreamThreads + threadIdx.x);
-                if (c < cells) {
-                    va[k] = __ldcg(reinterpret_cast<const float4 *>(d.tau[0][p] + c));
-                    vb[k] = __ldcg(reinterpret_cast<const float4 *>(d.tau[1][p] + c));
-                }
-            }
-        }
-        if (co < cells) *reinterpret_cast<uint4 *>(d.occ[p ^ 1] + co) = o;
-        if (aco) {
-            const float q = d.q;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const size_t c = c0 + 4 * ((size_t)k * kStreamThreads + threadIdx.x);
-                if (c < cells) {
-                    const float4 a4 = va[k], b4 = vb[k];
-                    *reinterpret_cast<float4 *>(d.tau[0][p ^ 1] + c) =
-                        make_float4(__fmul_rn(a4.x, q), __fmul_rn(a4.y, q), __fmul_rn(a4.z, q),
-                                    __fmul_rn(a4.w, q));
-                    *reinterpret_cast<float4 *>(d.tau[1][p ^ 1] + c) =
-                        make_float4(__fmul_rn(b4.x, q), __fmul_rn(b4.y, q), __fmul_rn(b4.z, q),
-                                    __fmul_rn(b4.w, q));
-                }
+        for (int k = 0; k < 4; ++k) {
+            const size_t c = c0 + 4 * ((size_t)k * kStreamThreads + threadIdx.x);
+            if (c < cells) {
+                va[k] = __ldcg(reinterpret_cast<const float4 *>(d.tau[0][p] + c));
+                vb[k] = __ldcg(reinterpret_cast<const float4 *>(d.tau[1][p] + c));
             }
         }
     }
-    // Complete only after the proposal pass has completed: the resolution
-    // pass waits for this kernel and then reads the proposals.
-    pdl_wait();
+    if (co < cells) *reinterpret_cast<uint4 *>(d.occ[p ^ 1] + co) = o;
+    if (aco) {
+        const float q = d.q;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const size_t c = c0 + 4 * ((size_t)k * kStreamThreads + threadIdx.x);
+            if (c < cells) {
+                const float4 a4 = va[k], b4 = vb[k];
+                *reinterpret_cast<float4 *>(d.tau[0][p ^ 1] + c) =
+                    make_float4(__fmul_rn(a4.x, q), __fmul_rn(a4.y, q), __fmul_rn(a4.z, q),
+                                __fmul_rn(a4.w, q));
+                *reinterpret_cast<float4 *>(d.tau[1][p ^ 1] + c) =
+                    make_float4(__fmul_rn(b4.x, q), __fmul_rn(b4.y, q), __fmul_rn(b4.z, q),
+                                __fmul_rn(b4.w, q));
+            }
+        }
+    }
+}
+
+static_assert(kStreamThreads == kAgentBlock, "both roles of the first kernel use one CTA size");
+
+// Called by every CTA of the last kernel of a step as its final action: the
+// last CTA to arrive (ticket) advances the step index of every scenario of
+// the work list (clamped at its end) and re-arms the ticket, so the next
+// step's kernels, which wait for this one, read the new index.
+__device__ __forceinline__ void finish_step(const ScenarioDesc *__restrict__ descs, int n_scen,
+                                            ActivityCtl *__restrict__ ctl)
+{
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    ScenarioDesc *md = const_cast<ScenarioDesc *>(descs);
+    for (int i = threadIdx.x; i < n_scen; i += blockDim.x) {
+        const unsigned long long v = md[i].step;
+        if (v < md[i].end_step) md[i].step = v + 1;
+    }
+    if (threadIdx.x == 0) ctl->ticket = 0u;
+    __threadfence();
 }
 
 __global__ void __launch_bounds__(kAgentBlock)
-agent_resolve_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__restrict__ agent_prefix,
-                     int n_scen, int t_off)
+agent_stage1_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__restrict__ cell_prefix,
+                    const uint32_t *__restrict__ agent_prefix, int n_scen, uint32_t cell_blocks,
+                    uint32_t agent_blocks)
 {
-    pdl_wait();  // streaming pass and, through it, proposal pass complete
+    // The state at t is the previous step's output: wait for it, then let
+    // the resolution kernel be scheduled (it waits for this one).
+    pdl_wait();
     pdl_trigger();
-    const int s = block_scenario(agent_prefix, n_scen, blockIdx.x);
-    const ScenarioDesc &d = descs[s];
-    const uint64_t t = d.step + (uint64_t)t_off;
-    const uint32_t blk = blockIdx.x - __ldg(agent_prefix + s);
-    const uint32_t a = blk * kAgentBlock + threadIdx.x;
-    Counts cnt;
-    if (t < d.end_step && a < 2u * d.n_per_side) {
-        // Two dependent rounds of loads: the agent's own entries, then its
-        // target's neighbourhood (every load of a round is in flight at once).
-        // Nothing read here is written by this kernel before it is read (the
-        // position and per-agent entries only by their own thread, after
-        // reading), so the loads take the read-only cached path.
-        const uint32_t id = a + 1u;
-        const uint32_t cell = __ldg(d.pos + id);
-        const int ac = __ldg(d.acode + id);
-        const bool aco = d.model == 1;
-        const bool tour_mode = aco && d.deposit_mode == 1;
-        const float tour0 = tour_mode ? __ldg(d.tour + id) : 0.0f;
-        const uint32_t arrived = __ldg(d.arrival + id);
-        const int code = ac & 15, g = ac >> 4;
-        if (code) {
-            const int W = d.W, H = d.H;
-            const int p = (int)(t & 1);
-            const uint8_t *occ = d.occ[p];
-            const int x = (int)(cell % (uint32_t)W), y = (int)(cell / (uint32_t)W);
-            const int dx = kCodeDX[code], dy = kCodeDY[code];
-            const int tx = x + dx, ty = y + dy;
-            const int64_t target = (int64_t)cell + (int64_t)dy * W + dx;
-            // the evaporated value of the target, recomputed from t (the
-            // streaming pass wrote the same value)
-            const float tau_t = aco ? __ldg(d.tau[g == 2 ? 1 : 0][p] + target) : 0.0f;
-            // Claim mask of the target: bit j when its neighbour at scan
-            // offset j is occupied at t and chose the target (code 8 - j).
-            uint32_t m = 0;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int ex = kCodeDX[j + 1], ey = kCodeDY[j + 1];
-                const int nx = tx + ex, ny = ty + ey;
-                if ((unsigned)nx >= (unsigned)W || (unsigned)ny >= (unsigned)H) continue;
-                const int64_t nc = target + (int64_t)ey * W + ex;
-                const int on = __ldg(occ + nc), pn = __ldg(d.prop + nc);
-                if (on != 0 && pn == 8 - j) m |= 1u << j;
-            }
-            const uint32_t k = (uint32_t)__popc(m);
-            const uint32_t mine = 8u - (uint32_t)code;  // this agent's scan offset
-            const uint32_t win =
-                k == 1 ? mine : pick_claimant(m, k, (uint64_t)target, t, d.seed);
-            if (win == mine) {
-                d.occ[p ^ 1][target] = (uint8_t)g;
-                d.occ[p ^ 1][cell] = 0;
-                d.pos[id] = (uint32_t)target;
-                d.ids[target] = id;
-                float dep = d.deposit;
-                if (tour_mode) {
-                    // Eq. 5: the tour length grows by the step length, then 1/L_k
-                    const float L = __fadd_rn(tour0, (dx != 0 && dy != 0) ? kSqrt2 : 1.0f);
-                    d.tour[id] = L;
-                    dep = __fdiv_rn(1.0f, L);
-                }
-                const bool in_band = g == 1 ? tx >= W - (int)d.band : tx < (int)d.band;
-                if (in_band && arrived == 0) {
-                    d.arrival[id] = (uint32_t)(t + 1);
-                    if (g == 1) ++cnt.crossed_a; else ++cnt.crossed_b;
-                }
-                if (aco)
-                    d.tau[g == 2 ? 1 : 0][p ^ 1][target] = __fadd_rn(__fmul_rn(tau_t, d.q), dep);
-                ++cnt.moved;
-                if (k >= 2) ++cnt.conflicts;
-            }
-        }
+    // CTA i is a proposal block when the count floor((i + 1) A / T) of
+    // proposal blocks among CTAs 0..i grows at i (A proposal blocks spread
+    // evenly over all T CTAs), else a stream block.
+    const uint64_t total = (uint64_t)cell_blocks + agent_blocks;
+    const uint32_t i = blockIdx.x;
+    const uint32_t na = (uint32_t)(((uint64_t)(i + 1) * agent_blocks) / total);
+    const uint32_t na_before = (uint32_t)(((uint64_t)i * agent_blocks) / total);
+    if (na == na_before) {
+        stream_block(descs, cell_prefix, n_scen, i - na);
+    } else {
+        const uint32_t b = na - 1;
+        const int s = block_scenario(agent_prefix, n_scen, b);
+        const ScenarioDesc &d = descs[s];
+        const uint64_t t = d.step;
+        const uint32_t a = (b - __ldg(agent_prefix + s)) * kAgentBlock + threadIdx.x;
+        if (t < d.end_step && a < 2u * d.n_per_side) propose_agent(d, a, t);
     }
-    flush_counts(d, cnt, blk % d.n_slots);
+}
+
+// Resolution work of one agent: its own entries (first round of loads) and
+// its target's neighbourhood (second round).  Nothing read here is written
+// by the resolution kernel before it is read (position and per-agent entries
+// only by their own thread, after reading), so the loads take the read-only
+// cached path and the rounds of several agents overlap.
+struct Resolve {
+    uint32_t id, cell;
+    int code, g;
+    float tour0;
+    uint32_t arrived;
+    int64_t target;
+    uint32_t mask;
+    float tau_t;
+};
+
+__device__ __forceinline__ void resolve_load_own(const ScenarioDesc &d, uint32_t a, Resolve &r)
+{
+    r.id = a + 1u;
+    r.cell = __ldg(d.pos + r.id);
+    const int ac = __ldg(d.acode + r.id);
+    r.code = ac & 15;
+    r.g = ac >> 4;
+    r.tour0 = (d.model == 1 && d.deposit_mode == 1) ? __ldg(d.tour + r.id) : 0.0f;
+    r.arrived = __ldg(d.arrival + r.id);
+}
+
+// Claim mask of the target (bit j: its claimant at scan offset j; every
+// claimant's proposal pass has OR-ed its bit in) and the target's own-group
+// pheromone at t.
+__device__ __forceinline__ void resolve_load_target(const ScenarioDesc &d, uint64_t t, Resolve &r)
+{
+    const int W = d.W;
+    const int p = (int)(t & 1);
+    r.target = (int64_t)r.cell + (int64_t)kCodeDY[r.code] * W + kCodeDX[r.code];
+    r.tau_t = d.model == 1 ? __ldg(d.tau[r.g == 2 ? 1 : 0][p] + r.target) : 0.0f;
+    r.mask = __ldg(d.claim[p] + r.target);
+}
+
+// The winner of the target (Sec. IV.d) and, if it is this agent, its move.
+__device__ __forceinline__ void resolve_apply(const ScenarioDesc &d, uint64_t t, const Resolve &r,
+                                              Counts &cnt)
+{
+    const uint32_t k = (uint32_t)__popc(r.mask);
+    const uint32_t mine = 8u - (uint32_t)r.code;  // this agent's scan offset
+    const uint32_t win = k == 1 ? mine : pick_claimant(r.mask, k, (uint64_t)r.target, t, d.seed);
+    if (win != mine) return;
+    const int W = d.W;
+    const int p = (int)(t & 1);
+    const int g = r.g;
+    const int dx = kCodeDX[r.code], dy = kCodeDY[r.code];
+    const int tx = (int)(r.cell % (uint32_t)W) + dx;
+    d.occ[p ^ 1][r.target] = (uint8_t)g;
+    d.occ[p ^ 1][r.cell] = 0;
+    d.pos[r.id] = (uint32_t)r.target;
+    d.acode[r.id] = (uint8_t)(r.code | (g << 4) | 0x80);
+    d.ids[r.target] = r.id;
+    float dep = d.deposit;
+    if (d.model == 1 && d.deposit_mode == 1) {
+        // Eq. 5: the tour length grows by the step length, then 1/L_k
+        const float L = __fadd_rn(r.tour0, (dx != 0 && dy != 0) ? kSqrt2 : 1.0f);
+        d.tour[r.id] = L;
+        dep = __fdiv_rn(1.0f, L);
+    }
+    const bool in_band = g == 1 ? tx >= W - (int)d.band : tx < (int)d.band;
+    if (in_band && r.arrived == 0) {
+        d.arrival[r.id] = (uint32_t)(t + 1);
+        if (g == 1) ++cnt.crossed_a; else ++cnt.crossed_b;
+    }
+    // the evaporated value (what the stream blocks wrote) plus the deposit
+    if (d.model == 1) d.tau[g == 2 ? 1 : 0][p ^ 1][r.target] = __fadd_rn(__fmul_rn(r.tau_t, d.q), dep);
+    ++cnt.moved;
+    if (k >= 2) ++cnt.conflicts;
+}
+
+// Each CTA resolves kResolveBlocks consecutive agent blocks, one agent of
+// each per thread, with the loads of all of them in flight together.
+#ifndef PEDSIM_RESOLVE_BLOCKS
+#define PEDSIM_RESOLVE_BLOCKS 1
+#endif
+constexpr int kResolveBlocks = PEDSIM_RESOLVE_BLOCKS;
+
+__global__ void __launch_bounds__(kAgentBlock)
+agent_resolve_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__restrict__ agent_prefix,
+                     int n_scen, uint32_t agent_blocks, ActivityCtl *__restrict__ ctl)
+{
+    pdl_wait();  // first kernel (proposals and stream) complete
+    pdl_trigger();
+    const ScenarioDesc *dq[kResolveBlocks];
+    uint32_t lb[kResolveBlocks];
+    bool live[kResolveBlocks];
+    Resolve r[kResolveBlocks];
+#pragma unroll
+    for (int q = 0; q < kResolveBlocks; ++q) {
+        const uint32_t b = blockIdx.x * kResolveBlocks + q;
+        live[q] = false;
+        dq[q] = descs;
+        lb[q] = 0;
+        if (b >= agent_blocks) continue;
+        const int s = block_scenario(agent_prefix, n_scen, b);
+        dq[q] = descs + s;
+        lb[q] = b - __ldg(agent_prefix + s);
+        const uint32_t a = lb[q] * kAgentBlock + threadIdx.x;
+        live[q] = dq[q]->step < dq[q]->end_step && a < 2u * dq[q]->n_per_side;
+        if (live[q]) resolve_load_own(*dq[q], a, r[q]);
+        if (live[q] && r[q].code == 0) live[q] = false;
+    }
+#pragma unroll
+    for (int q = 0; q < kResolveBlocks; ++q)
+        if (live[q]) resolve_load_target(*dq[q], dq[q]->step, r[q]);
+#pragma unroll
+    for (int q = 0; q < kResolveBlocks; ++q) {
+        Counts cnt;
+        if (live[q]) resolve_apply(*dq[q], dq[q]->step, r[q], cnt);
+        if (blockIdx.x * kResolveBlocks + q < agent_blocks)
+            flush_counts(*dq[q], cnt, lb[q] % dq[q]->n_slots);
+    }
+    finish_step(descs, n_scen, ctl);
 }
 
 __global__ void build_pos_kernel(const ScenarioDesc *__restrict__ dp)
@@ -215,25 +310,31 @@ __global__ void build_pos_kernel(const ScenarioDesc *__restrict__ dp)
     const ScenarioDesc &d = *dp;
     const size_t cells = (size_t)d.W * (size_t)d.H;
     const uint8_t *occ = d.occ[d.step & 1];
-    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells;
-         c += (size_t)gridDim.x * blockDim.x)
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells; c += stride) {
+        d.claim[0][c] = 0;
+        d.claim[1][c] = 0;
         if (occ[c]) d.pos[d.ids[c]] = (uint32_t)c;
+    }
+    const size_t agents = 2 * (size_t)d.n_per_side + 1;
+    for (size_t a = (size_t)blockIdx.x * blockDim.x + threadIdx.x; a < agents; a += stride)
+        d.acode[a] = 0;
 }
 
 cudaError_t launch_agent_step(const ScenarioDesc *d_descs, const uint32_t *d_cell_prefix,
                               const uint32_t *d_agent_prefix, int n, uint32_t cell_blocks,
-                              uint32_t agent_blocks, int t_off, cudaStream_t stream)
+                              uint32_t agent_blocks, ActivityCtl *ctl, cudaStream_t stream)
 {
     if (n <= 0 || cell_blocks == 0) return cudaSuccess;
-    // with no agent the proposal pass is one CTA that only orders the stream
-    cudaError_t e = launch_pdl(agent_propose_kernel, agent_blocks ? agent_blocks : 1u,
-                               (unsigned)kAgentBlock, stream, d_descs, d_agent_prefix, n, t_off);
+    cudaError_t e = launch_pdl(agent_stage1_kernel, cell_blocks + agent_blocks,
+                               (unsigned)kAgentBlock, stream, d_descs, d_cell_prefix,
+                               d_agent_prefix, n, cell_blocks, agent_blocks);
     if (e != cudaSuccess) return e;
-    e = launch_pdl(stream_kernel, cell_blocks, (unsigned)kStreamThreads, stream, d_descs,
-                   d_cell_prefix, n, t_off);
-    if (e != cudaSuccess || agent_blocks == 0) return e;
-    return launch_pdl(agent_resolve_kernel, agent_blocks, (unsigned)kAgentBlock, stream, d_descs,
-                      d_agent_prefix, n, t_off);
+    // the resolution kernel also advances the step index: with no agent it
+    // is one CTA that does only that
+    const uint32_t g = agent_blocks ? (agent_blocks + kResolveBlocks - 1) / kResolveBlocks : 1u;
+    return launch_pdl(agent_resolve_kernel, g, (unsigned)kAgentBlock, stream, d_descs,
+                      d_agent_prefix, n, agent_blocks, ctl);
 }
 
 cudaError_t launch_build_pos(const ScenarioDesc *d_desc, int cells, cudaStream_t stream)

@@ -24,8 +24,8 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // Device memory layout of one scenario (one allocation)
 // ---------------------------------------------------------------------------
 struct Layout {
-    size_t desc, occ[2], prop, ids, tau[2][2], arrival, tour, pos, acode, part, error, prefix,
-        counts, totals, act, act_bytes;
+    size_t desc, occ[2], prop, claim, ids, tau[2][2], arrival, tour, pos, acode, part, error,
+        prefix, counts, totals, act, act_bytes;
     size_t total;
     uint32_t n_slots;
     bool has_tau, has_tour;
@@ -70,6 +70,7 @@ Layout make_layout(int W, int H, const sim_params &p)
     L.occ[0] = take(cells);
     L.occ[1] = take(cells);
     L.prop = take(cells);  // proposal plane of the two-kernel step variants
+    L.claim = take(2 * cells);  // claim-mask planes of the agent-parallel variant
     L.ids = take(4 * cells);
     for (int g = 0; g < 2; ++g)
         for (int q = 0; q < 2; ++q) L.tau[g][q] = L.has_tau ? take(4 * cells) : 0;
@@ -220,6 +221,8 @@ int upload_desc(sim_t *s)
     d.occ[0] = m + L.occ[0];
     d.occ[1] = m + L.occ[1];
     d.prop = m + L.prop;
+    d.claim[0] = m + L.claim;
+    d.claim[1] = m + L.claim + (size_t)s->W * (size_t)s->H;
     d.ids = reinterpret_cast<uint32_t *>(m + L.ids);
     for (int g = 0; g < 2; ++g)
         for (int q = 0; q < 2; ++q)
@@ -318,9 +321,10 @@ int launch_one_step(sim_t *s, int t_off, cudaStream_t st)
         return PEDSIM_OK;
     }
     if (s->variant == kVariantAgent) {
+        // the agent step reads and advances the step index itself
         SIM_CUDA(s, launch_agent_step(s->d_desc, s->d_prefix + 2, s->d_prefix + 4, 1,
                                       cell_blocks(s->W, s->H), agent_blocks(s->p.n_per_side),
-                                      t_off, st));
+                                      s->d_act, st));
         return PEDSIM_OK;
     }
     SIM_CUDA(s, launch_fused_step(s->d_desc, s->d_prefix, 1, total, t_off, s->tile_w, s->tile_h,
@@ -336,7 +340,7 @@ int ensure_graph(sim_t *s)
     SIM_CUDA(s, cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
     int rc = PEDSIM_OK;
     for (int k = 0; k < kGraphSteps && rc == PEDSIM_OK; ++k) rc = launch_one_step(s, k, s->cap);
-    if (rc == PEDSIM_OK) {
+    if (rc == PEDSIM_OK && s->variant != kVariantAgent) {
         cudaError_t ea = launch_advance(s->d_desc, 1, kGraphSteps, s->cap);
         if (ea != cudaSuccess) rc = cuda_fail(s, ea, "advance kernel capture");
     }
@@ -492,7 +496,8 @@ int sim_step(sim_t *s, int n)
             int rc = launch_one_step(s, k, s->stream);
             if (rc != PEDSIM_OK) return rc;
         }
-        SIM_CUDA(s, launch_advance(s->d_desc, 1, rem, s->stream));
+        if (s->variant != kVariantAgent)
+            SIM_CUDA(s, launch_advance(s->d_desc, 1, rem, s->stream));
     }
     s->step += (unsigned long long)n;
     return PEDSIM_OK;
@@ -887,10 +892,11 @@ struct MultiRun {
                                         d_act, st)
                 : variant == kVariantAgent
                     ? launch_agent_step(d_descs, d_prefix + (n + 1), d_prefix + 2 * (n + 1), count,
-                                        cell_total, agent_total, i, st)
+                                        cell_total, agent_total, d_act, st)
                     : launch_pipeline_step(d_descs, d_prefix, count, total, i, tile_h, st);
             if (e != cudaSuccess) return cuda_(e, "batched step launch");
         }
+        if (variant == kVariantAgent) return PEDSIM_OK;  // the step advanced itself
         cudaError_t e = launch_advance(d_descs, count, k, st);
         if (e != cudaSuccess) return cuda_(e, "advance launch");
         return PEDSIM_OK;

@@ -36,7 +36,12 @@ namespace pedsim {
 //                 parallel variant; rebuilt from the planes whenever the
 //                 state is set from outside it)
 //   acode         uint8 per agent: proposal code | group << 4 of the current
-//                 step (agent-parallel variant)
+//                 step, | 0x80 once the agent has moved (agent-parallel
+//                 variant)
+//   claim[q]      uint8 claim-mask planes of the agent-parallel variant: at
+//                 step t, claim[t & 1] holds at each target cell bit j for
+//                 its claimant at scan offset j; the other plane is cleared
+//                 at the previous step's targets during the same step
 constexpr int kDescHeaderBytes = 256;
 
 struct alignas(128) ScenarioDesc {
@@ -64,7 +69,8 @@ struct alignas(128) ScenarioDesc {
     int *error;
     uint32_t *pos;
     uint8_t *acode;
-    uint8_t header_pad_[kDescHeaderBytes - 96 - 14 * 8];
+    uint8_t *claim[2];
+    uint8_t header_pad_[kDescHeaderBytes - 96 - 16 * 8];
     // TMA tensor maps; boxes follow the variant and tile shape:
     //   tiled two-kernel step: occ (tile_w + 32) x (tile_h + 2), occ_out and
     //   prop_out tile_w x tile_h, prop (tile_w + 32) x (tile_h + 4), tau
@@ -90,7 +96,7 @@ static_assert(sizeof(ScenarioDesc) == kDescHeaderBytes + 14 * sizeof(CUtensorMap
 // `reset` = nonzero after the host changes the work list or a state: that
 // launch treats every tile as active.
 struct ActivityCtl {
-    uint32_t ticket;    // elects the launch's last CTA
+    uint32_t ticket;    // elects the launch's last CTA (fused and agent variants)
     uint32_t work;      // next entry of the active list to hand out
     uint32_t phase;     // launch index mod 3
     uint32_t reset;
@@ -142,13 +148,17 @@ cudaError_t launch_pipeline_step(const ScenarioDesc *d_descs, const uint32_t *d_
 int two_pass_grid(int W, int H);
 cudaError_t launch_two_pass_step(const ScenarioDesc *d_desc, uint8_t *d_prop, int W, int H,
                                  int t_off, cudaStream_t stream);
-// Agent-parallel step over scenarios [0, n): cell_prefix[i] / agent_prefix[i]
-// = first streaming / agent CTA of scenario i (ceil(W*H / kCellBlock) and
-// ceil(2 n_per_side / kAgentBlock) per scenario), [n] = the totals.
+// Agent-parallel step over scenarios [0, n) at each scenario's step index,
+// which the step advances itself (no launch_advance for this variant):
+// cell_prefix[i] / agent_prefix[i] = first cell / agent block of scenario i
+// (ceil(W*H / kCellBlock) and ceil(2 n_per_side / kAgentBlock) per
+// scenario), [n] = the totals.  ctl->ticket (zero between launches) elects
+// the CTA that advances the step indices.
 cudaError_t launch_agent_step(const ScenarioDesc *d_descs, const uint32_t *d_cell_prefix,
                               const uint32_t *d_agent_prefix, int n, uint32_t cell_blocks,
-                              uint32_t agent_blocks, int t_off, cudaStream_t stream);
-// Rebuilds pos[] of one scenario from its planes at its current step.
+                              uint32_t agent_blocks, ActivityCtl *ctl, cudaStream_t stream);
+// Rebuilds pos[] of one scenario from its planes at its current step and
+// clears its claim planes and per-agent codes (agent-parallel variant).
 cudaError_t launch_build_pos(const ScenarioDesc *d_desc, int cells, cudaStream_t stream);
 // step += k (clamped at end_step) for scenarios [0, n).
 cudaError_t launch_advance(const ScenarioDesc *d_descs, int n, int k, cudaStream_t stream);
