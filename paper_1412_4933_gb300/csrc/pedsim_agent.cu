@@ -7,9 +7,9 @@
 //                         rule (Eq. 1 LEM rank draw, Eq. 2 ACO roulette) from
 //                         the occupancy and pheromone at t; the direction code
 //                         goes to the agent's cell of the proposal plane
-//     stream blocks       every cell: occupancy copied to the plane of t+1,
-//                         both pheromone planes evaporated (Eq. 3); a pure
-//                         16-byte-vector stream, the HBM-bound part of the step
+//     stream blocks       every cell: both pheromone planes evaporated into
+//                         the planes of t+1 (Eq. 3); a pure 16-byte-vector
+//                         stream, the HBM-bound part of the step (ACO only)
 //   agent_resolve_kernel  one thread per agent with a proposal: the claimants
 //                         of its target cell are read back from the proposal
 //                         plane (codes are valid exactly at cells occupied at
@@ -18,8 +18,11 @@
 //                         and arrival, and its deposit (Eq. 4/5) on top of the
 //                         evaporated value
 //
-// The two roles write disjoint outputs, so the proposals run inside the
-// stream instead of before it.  The resolution kernel is chained by
+// Occupancy lives in one plane, occ[0], updated in place: the proposals read
+// it (state at t) in the first kernel, the moves are applied to it only in
+// the second, and no other cell changes.  The two roles of the first kernel
+// write disjoint outputs, so the proposals run inside the stream instead of
+// before it.  The resolution kernel is chained by
 // programmatic dependent launch: the first kernel releases it as soon as all
 // of its CTAs have started, so its CTAs are resident before the first kernel
 // ends, and it waits for the first kernel's completion.  The last CTA of
@@ -59,7 +62,7 @@ __device__ __forceinline__ void propose_agent(const ScenarioDesc &d, uint32_t a,
     const int prev = __ldg(d.acode + id);
     const int x = (int)(cell % (uint32_t)W), y = (int)(cell / (uint32_t)W);
     const int p = (int)(t & 1);
-    const uint8_t *occ = d.occ[p];
+    const uint8_t *occ = d.occ[0];
     const int g = __ldg(occ + cell);
     const float *tp = d.tau[g == 2 ? 1 : 0][p];
     const RuleParams rp{d.model, d.alpha, d.beta, d.lem_scale};
@@ -83,8 +86,8 @@ __device__ __forceinline__ void propose_agent(const ScenarioDesc &d, uint32_t a,
     d.acode[id] = (uint8_t)(code | (g << 4));
 }
 
-// Occupancy copy and evaporation of cell block b (kCellBlock cells) of the
-// work list.  Reads bypass L1 (.cg): the data is streamed once.
+// Evaporation of cell block b (kCellBlock cells) of the work list's
+// pheromone.  Reads bypass L1 (.cg): the data is streamed once.
 __device__ __forceinline__ void stream_block(const ScenarioDesc *__restrict__ descs,
                                              const uint32_t *__restrict__ cell_prefix, int n_scen,
                                              uint32_t b)
@@ -96,38 +99,29 @@ __device__ __forceinline__ void stream_block(const ScenarioDesc *__restrict__ de
     const size_t cells = (size_t)d.W * (size_t)d.H;
     const size_t c0 = (size_t)(b - __ldg(cell_prefix + s)) * kCellBlock;
     const int p = (int)(t & 1);
-    const bool aco = d.model == 1;
-    // occupancy: 16 cells per thread; pheromone: 4 float4 per plane and
-    // thread, consecutive threads on consecutive vectors
-    const size_t co = c0 + 16 * (size_t)threadIdx.x;
-    uint4 o = make_uint4(0u, 0u, 0u, 0u);
-    if (co < cells) o = __ldcg(reinterpret_cast<const uint4 *>(d.occ[p] + co));
+    // 4 float4 per plane and thread, consecutive threads on consecutive
+    // vectors; every load of the block is in flight before the first store
     float4 va[4], vb[4];
-    if (aco) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const size_t c = c0 + 4 * ((size_t)k * kStreamThreads + threadIdx.x);
-            if (c < cells) {
-                va[k] = __ldcg(reinterpret_cast<const float4 *>(d.tau[0][p] + c));
-                vb[k] = __ldcg(reinterpret_cast<const float4 *>(d.tau[1][p] + c));
-            }
+    for (int k = 0; k < 4; ++k) {
+        const size_t c = c0 + 4 * ((size_t)k * kStreamThreads + threadIdx.x);
+        if (c < cells) {
+            va[k] = __ldcg(reinterpret_cast<const float4 *>(d.tau[0][p] + c));
+            vb[k] = __ldcg(reinterpret_cast<const float4 *>(d.tau[1][p] + c));
         }
     }
-    if (co < cells) *reinterpret_cast<uint4 *>(d.occ[p ^ 1] + co) = o;
-    if (aco) {
-        const float q = d.q;
+    const float q = d.q;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const size_t c = c0 + 4 * ((size_t)k * kStreamThreads + threadIdx.x);
-            if (c < cells) {
-                const float4 a4 = va[k], b4 = vb[k];
-                *reinterpret_cast<float4 *>(d.tau[0][p ^ 1] + c) =
-                    make_float4(__fmul_rn(a4.x, q), __fmul_rn(a4.y, q), __fmul_rn(a4.z, q),
-                                __fmul_rn(a4.w, q));
-                *reinterpret_cast<float4 *>(d.tau[1][p ^ 1] + c) =
-                    make_float4(__fmul_rn(b4.x, q), __fmul_rn(b4.y, q), __fmul_rn(b4.z, q),
-                                __fmul_rn(b4.w, q));
-            }
+    for (int k = 0; k < 4; ++k) {
+        const size_t c = c0 + 4 * ((size_t)k * kStreamThreads + threadIdx.x);
+        if (c < cells) {
+            const float4 a4 = va[k], b4 = vb[k];
+            *reinterpret_cast<float4 *>(d.tau[0][p ^ 1] + c) =
+                make_float4(__fmul_rn(a4.x, q), __fmul_rn(a4.y, q), __fmul_rn(a4.z, q),
+                            __fmul_rn(a4.w, q));
+            *reinterpret_cast<float4 *>(d.tau[1][p ^ 1] + c) =
+                make_float4(__fmul_rn(b4.x, q), __fmul_rn(b4.y, q), __fmul_rn(b4.z, q),
+                            __fmul_rn(b4.w, q));
         }
     }
 }
@@ -237,8 +231,8 @@ __device__ __forceinline__ void resolve_apply(const ScenarioDesc &d, uint64_t t,
     const int g = r.g;
     const int dx = kCodeDX[r.code], dy = kCodeDY[r.code];
     const int tx = (int)(r.cell % (uint32_t)W) + dx;
-    d.occ[p ^ 1][r.target] = (uint8_t)g;
-    d.occ[p ^ 1][r.cell] = 0;
+    d.occ[0][r.target] = (uint8_t)g;
+    d.occ[0][r.cell] = 0;
     d.pos[r.id] = (uint32_t)r.target;
     d.acode[r.id] = (uint8_t)(r.code | (g << 4) | 0x80);
     d.ids[r.target] = r.id;
@@ -305,11 +299,11 @@ agent_resolve_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__r
     finish_step(descs, n_scen, ctl);
 }
 
-__global__ void build_pos_kernel(const ScenarioDesc *__restrict__ dp)
+__global__ void build_pos_kernel(const ScenarioDesc *__restrict__ dp, int plane)
 {
     const ScenarioDesc &d = *dp;
     const size_t cells = (size_t)d.W * (size_t)d.H;
-    const uint8_t *occ = d.occ[d.step & 1];
+    const uint8_t *occ = d.occ[plane];
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells; c += stride) {
         d.claim[0][c] = 0;
@@ -325,11 +319,13 @@ cudaError_t launch_agent_step(const ScenarioDesc *d_descs, const uint32_t *d_cel
                               const uint32_t *d_agent_prefix, int n, uint32_t cell_blocks,
                               uint32_t agent_blocks, ActivityCtl *ctl, cudaStream_t stream)
 {
-    if (n <= 0 || cell_blocks == 0) return cudaSuccess;
-    cudaError_t e = launch_pdl(agent_stage1_kernel, cell_blocks + agent_blocks,
-                               (unsigned)kAgentBlock, stream, d_descs, d_cell_prefix,
-                               d_agent_prefix, n, cell_blocks, agent_blocks);
-    if (e != cudaSuccess) return e;
+    if (n <= 0) return cudaSuccess;
+    if (cell_blocks + agent_blocks) {
+        cudaError_t e = launch_pdl(agent_stage1_kernel, cell_blocks + agent_blocks,
+                                   (unsigned)kAgentBlock, stream, d_descs, d_cell_prefix,
+                                   d_agent_prefix, n, cell_blocks, agent_blocks);
+        if (e != cudaSuccess) return e;
+    }
     // the resolution kernel also advances the step index: with no agent it
     // is one CTA that does only that
     const uint32_t g = agent_blocks ? (agent_blocks + kResolveBlocks - 1) / kResolveBlocks : 1u;
@@ -337,12 +333,12 @@ cudaError_t launch_agent_step(const ScenarioDesc *d_descs, const uint32_t *d_cel
                       d_agent_prefix, n, agent_blocks, ctl);
 }
 
-cudaError_t launch_build_pos(const ScenarioDesc *d_desc, int cells, cudaStream_t stream)
+cudaError_t launch_build_pos(const ScenarioDesc *d_desc, int cells, int plane, cudaStream_t stream)
 {
     int blocks = (cells + 255) / 256;
     if (blocks > 1024) blocks = 1024;
     if (blocks < 1) blocks = 1;
-    build_pos_kernel<<<blocks, 256, 0, stream>>>(d_desc);
+    build_pos_kernel<<<blocks, 256, 0, stream>>>(d_desc, plane);
     return cudaGetLastError();
 }
 

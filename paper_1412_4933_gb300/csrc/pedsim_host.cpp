@@ -200,9 +200,11 @@ void drop_graph(sim_t *s)
 
 int tiles_of(int n, int t) { return (n + t - 1) / t; }
 
-// Work blocks of the agent-parallel variant.
-uint32_t cell_blocks(int W, int H)
+// Work blocks of the agent-parallel variant: pheromone stream blocks (none
+// for LEM, which keeps no pheromone) and agent blocks.
+uint32_t cell_blocks(int W, int H, const sim_params &p)
 {
+    if (p.model != PEDSIM_ACO) return 0;
     return (uint32_t)(((size_t)W * (size_t)H + kCellBlock - 1) / kCellBlock);
 }
 uint32_t agent_blocks(uint32_t n_per_side)
@@ -286,8 +288,8 @@ int upload_desc(sim_t *s)
                                          d.tau[g][q], s->W, s->H, TWd, THd);
         if (!ok) return fail(s, PEDSIM_ECUDA, "cuTensorMapEncodeTiled failed (tiled variant)");
     }
-    const uint32_t prefix[6] = {0u, (uint32_t)(d.tiles_x * d.tiles_y), 0u, cell_blocks(s->W, s->H),
-                                0u, agent_blocks(s->p.n_per_side)};
+    const uint32_t prefix[6] = {0u, (uint32_t)(d.tiles_x * d.tiles_y), 0u,
+                                cell_blocks(s->W, s->H, s->p), 0u, agent_blocks(s->p.n_per_side)};
     // the handle's own descriptor becomes the live one again (a work list that
     // held it re-uploads its copy when it runs next)
     s->d_desc = s->own_desc;
@@ -323,7 +325,7 @@ int launch_one_step(sim_t *s, int t_off, cudaStream_t st)
     if (s->variant == kVariantAgent) {
         // the agent step reads and advances the step index itself
         SIM_CUDA(s, launch_agent_step(s->d_desc, s->d_prefix + 2, s->d_prefix + 4, 1,
-                                      cell_blocks(s->W, s->H), agent_blocks(s->p.n_per_side),
+                                      cell_blocks(s->W, s->H, s->p), agent_blocks(s->p.n_per_side),
                                       s->d_act, st));
         return PEDSIM_OK;
     }
@@ -379,6 +381,37 @@ bool params_ok(int W, int H, const sim_params *p)
 }
 
 size_t agents_len(const sim_t *s) { return 2 * (size_t)s->p.n_per_side + 1; }
+
+// Occupancy plane that holds the current state: the agent-parallel variant
+// updates plane 0 in place, the others alternate by step parity.
+int occ_plane(const sim_t *s, int variant, unsigned long long step)
+{
+    (void)s;
+    return variant == kVariantAgent ? 0 : (int)(step & 1);
+}
+int occ_plane(const sim_t *s) { return occ_plane(s, s->variant, s->step); }
+
+// Changes the step variant and tiling of a scenario between steps: the
+// occupancy moves to the plane the new variant keeps it in, and the agent
+// positions are rebuilt when the new variant is the agent-parallel one (only
+// that variant keeps them up to date).
+int switch_variant(sim_t *s, int variant, int tw, int th, int cps)
+{
+    const int from = occ_plane(s), to = occ_plane(s, variant, s->step);
+    if (from != to)
+        SIM_CUDA(s, cudaMemcpyAsync(s->hdesc.occ[to], s->hdesc.occ[from],
+                                    (size_t)s->W * (size_t)s->H, cudaMemcpyDeviceToDevice,
+                                    s->stream));
+    const int old = s->variant;
+    s->variant = variant;
+    s->tile_w = tw;
+    s->tile_h = th;
+    s->ctas_per_sm = cps;
+    int rc = upload_desc(s);
+    if (rc == PEDSIM_OK && variant == kVariantAgent && old != kVariantAgent)
+        SIM_CUDA(s, launch_build_pos(s->d_desc, s->W * s->H, to, s->stream));
+    return rc;
+}
 
 }  // namespace
 
@@ -476,7 +509,7 @@ int sim_place(sim_t *s, uint64_t seed)
     if (rc != PEDSIM_OK) return rc;
     SIM_CUDA(s, launch_init(s->d_desc, 1, s->W * s->H, (int)agents_len(s), s->stream));
     SIM_CUDA(s, launch_place(s->d_desc, 1, s->stream));
-    SIM_CUDA(s, launch_build_pos(s->d_desc, s->W * s->H, s->stream));
+    SIM_CUDA(s, launch_build_pos(s->d_desc, s->W * s->H, 0, s->stream));
     return PEDSIM_OK;
 }
 
@@ -508,6 +541,7 @@ int sim_read_grid(sim_t *s, uint8_t *occ, uint32_t *ids, float *tauA, float *tau
     if (!s) return PEDSIM_EINVAL;
     const size_t cells = (size_t)s->W * s->H;
     const int par = (int)(s->step & 1);
+    const int oplane = occ_plane(s);
     std::vector<uint8_t> occ_tmp;
     uint8_t *occ_h = occ;
     if (ids && !occ) {
@@ -515,7 +549,8 @@ int sim_read_grid(sim_t *s, uint8_t *occ, uint32_t *ids, float *tauA, float *tau
         occ_h = occ_tmp.data();
     }
     if (occ_h)
-        SIM_CUDA(s, cudaMemcpyAsync(occ_h, s->hdesc.occ[par], cells, cudaMemcpyDeviceToHost, s->stream));
+        SIM_CUDA(s, cudaMemcpyAsync(occ_h, s->hdesc.occ[oplane], cells, cudaMemcpyDeviceToHost,
+                                    s->stream));
     if (ids)
         SIM_CUDA(s, cudaMemcpyAsync(ids, s->hdesc.ids, 4 * cells, cudaMemcpyDeviceToHost, s->stream));
     float *dst[2] = {tauA, tauB};
@@ -570,7 +605,9 @@ int sim_set_state(sim_t *s, uint64_t seed, uint64_t step, const uint8_t *occ, co
     if (rc != PEDSIM_OK) return rc;
     SIM_CUDA(s, launch_init(s->d_desc, 1, s->W * s->H, (int)agents_len(s), s->stream));
     const int par = (int)(step & 1);
-    SIM_CUDA(s, cudaMemcpyAsync(s->hdesc.occ[par], occ, cells, cudaMemcpyHostToDevice, s->stream));
+    const int oplane = occ_plane(s);
+    SIM_CUDA(s, cudaMemcpyAsync(s->hdesc.occ[oplane], occ, cells, cudaMemcpyHostToDevice,
+                                s->stream));
     SIM_CUDA(s, cudaMemcpyAsync(s->hdesc.ids, ids, 4 * cells, cudaMemcpyHostToDevice, s->stream));
     if (s->L.has_tau) {
         const float *src[2] = {tauA, tauB};
@@ -587,7 +624,7 @@ int sim_set_state(sim_t *s, uint64_t seed, uint64_t step, const uint8_t *occ, co
         SIM_CUDA(s, cudaMemcpyAsync(s->hdesc.arrival, arrival, 4 * na, cudaMemcpyHostToDevice, s->stream));
     if (tour && s->L.has_tour)
         SIM_CUDA(s, cudaMemcpyAsync(s->hdesc.tour, tour, 4 * na, cudaMemcpyHostToDevice, s->stream));
-    SIM_CUDA(s, launch_build_pos(s->d_desc, s->W * s->H, s->stream));
+    SIM_CUDA(s, launch_build_pos(s->d_desc, s->W * s->H, oplane, s->stream));
     return PEDSIM_OK;
 }
 
@@ -596,7 +633,7 @@ int sim_stats(sim_t *s, sim_stats_t *out)
     if (!s || !out) return PEDSIM_EINVAL;
     unsigned long long ctr[kNumCounters], dstep = 0;
     unsigned int counts[kGridCounts];
-    const int par = (int)(s->step & 1);
+    const int par = occ_plane(s);
     unsigned int *d_counts = reinterpret_cast<unsigned int *>(s->dmem + s->L.counts);
     unsigned long long *d_tot = reinterpret_cast<unsigned long long *>(s->dmem + s->L.totals);
     SIM_CUDA(s, launch_grid_counts(s->d_desc, par, s->W * s->H, d_counts, s->stream));
@@ -726,16 +763,8 @@ int sim_set_variant(sim_t *s, int variant)
                variant != kVariantFused && variant != kVariantAgent))
         return fail(s, PEDSIM_EINVAL, "unknown variant");
     if (variant == s->variant) return PEDSIM_OK;
-    s->variant = variant;
     // each variant starts from its own default tile shape
-    s->tile_w = variant == kVariantFused ? 64 : 128;
-    s->tile_h = 16;
-    s->ctas_per_sm = 0;
-    int rc = upload_desc(s);
-    // agent positions are kept up to date by the agent-parallel variant only
-    if (rc == PEDSIM_OK && variant == kVariantAgent)
-        SIM_CUDA(s, launch_build_pos(s->d_desc, s->W * s->H, s->stream));
-    return rc;
+    return switch_variant(s, variant, variant == kVariantFused ? 64 : 128, 16, 0);
 }
 
 int sim_set_tiling(sim_t *s, int tile_w, int tile_h, int ctas_per_sm)
@@ -838,7 +867,7 @@ struct MultiRun {
         for (size_t i = 0; i < n; ++i) {
             h[i] = sims[i]->hdesc;
             pre[i + 1] = pre[i] + (uint32_t)(h[i].tiles_x * h[i].tiles_y);
-            pre[n + 1 + i + 1] = pre[n + 1 + i] + cell_blocks(sims[i]->W, sims[i]->H);
+            pre[n + 1 + i + 1] = pre[n + 1 + i] + cell_blocks(sims[i]->W, sims[i]->H, sims[i]->p);
             pre[2 * (n + 1) + i + 1] = pre[2 * (n + 1) + i] + agent_blocks(sims[i]->p.n_per_side);
         }
         count = (int)n;
@@ -945,11 +974,7 @@ struct MultiRun {
 
 int retile(sim_t *s, int variant, int tw, int th, int cps)
 {
-    s->variant = variant;
-    s->tile_w = tw;
-    s->tile_h = th;
-    s->ctas_per_sm = cps;
-    return upload_desc(s);
+    return switch_variant(s, variant, tw, th, cps);
 }
 
 }  // namespace
@@ -1061,10 +1086,6 @@ int sim_batch_set_variant(batch_t *b, int variant)
     const int tw = variant == kVariantFused ? 64 : 128;
     for (sim_t *s : b->sims) {
         int rc = retile(s, variant, tw, 16, 0);
-        if (rc == PEDSIM_OK && variant == kVariantAgent) {
-            cudaError_t e = launch_build_pos(s->d_desc, s->W * s->H, s->stream);
-            if (e != cudaSuccess) rc = cuda_fail(s, e, "position rebuild");
-        }
         if (rc) { b->run.err = s->err; return rc; }
     }
     b->run.tile_w = tw;

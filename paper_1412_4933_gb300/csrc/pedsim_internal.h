@@ -22,7 +22,8 @@ namespace pedsim {
 //                 replays at any step
 //   end_step      the scenario does not advance past this step
 //   occ[p]        uint8 occupancy plane of parity p (state at step t lives in
-//                 occ[t & 1])
+//                 occ[t & 1]; the agent-parallel variant updates occ[0] in
+//                 place at every step)
 //   prop          uint8 proposal plane (two-kernel variants)
 //   tau[g][p]     float pheromone plane of group g (0 = A, 1 = B), parity p
 //   ids           uint32 agent-id plane, updated in place (a move reads the
@@ -157,9 +158,10 @@ cudaError_t launch_two_pass_step(const ScenarioDesc *d_desc, uint8_t *d_prop, in
 cudaError_t launch_agent_step(const ScenarioDesc *d_descs, const uint32_t *d_cell_prefix,
                               const uint32_t *d_agent_prefix, int n, uint32_t cell_blocks,
                               uint32_t agent_blocks, ActivityCtl *ctl, cudaStream_t stream);
-// Rebuilds pos[] of one scenario from its planes at its current step and
-// clears its claim planes and per-agent codes (agent-parallel variant).
-cudaError_t launch_build_pos(const ScenarioDesc *d_desc, int cells, cudaStream_t stream);
+// Rebuilds pos[] of one scenario from its occupancy plane `plane` and clears
+// its claim planes and per-agent codes (agent-parallel variant).
+cudaError_t launch_build_pos(const ScenarioDesc *d_desc, int cells, int plane,
+                             cudaStream_t stream);
 // step += k (clamped at end_step) for scenarios [0, n).
 cudaError_t launch_advance(const ScenarioDesc *d_descs, int n, int k, cudaStream_t stream);
 // out[0..3] = counter totals of one scenario (sums over its slots).
