@@ -128,30 +128,6 @@ __device__ __forceinline__ void stream_block(const ScenarioDesc *__restrict__ de
 
 static_assert(kStreamThreads == kAgentBlock, "both roles of the first kernel use one CTA size");
 
-// Called by every CTA of the last kernel of a step as its final action: the
-// last CTA to arrive (ticket) advances the step index of every scenario of
-// the work list (clamped at its end) and re-arms the ticket, so the next
-// step's kernels, which wait for this one, read the new index.
-__device__ __forceinline__ void finish_step(const ScenarioDesc *__restrict__ descs, int n_scen,
-                                            ActivityCtl *__restrict__ ctl)
-{
-    __shared__ bool last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    ScenarioDesc *md = const_cast<ScenarioDesc *>(descs);
-    for (int i = threadIdx.x; i < n_scen; i += blockDim.x) {
-        const unsigned long long v = md[i].step;
-        if (v < md[i].end_step) md[i].step = v + 1;
-    }
-    if (threadIdx.x == 0) ctl->ticket = 0u;
-    __threadfence();
-}
-
 __global__ void __launch_bounds__(kAgentBlock)
 agent_stage1_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__restrict__ cell_prefix,
                     const uint32_t *__restrict__ agent_prefix, int n_scen, uint32_t cell_blocks,
@@ -269,6 +245,7 @@ agent_resolve_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__r
     pdl_trigger();
     const ScenarioDesc *dq[kResolveBlocks];
     uint32_t lb[kResolveBlocks];
+    uint64_t tq[kResolveBlocks];
     bool live[kResolveBlocks];
     Resolve r[kResolveBlocks];
 #pragma unroll
@@ -277,27 +254,47 @@ agent_resolve_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__r
         live[q] = false;
         dq[q] = descs;
         lb[q] = 0;
+        tq[q] = 0;
         if (b >= agent_blocks) continue;
         const int s = block_scenario(agent_prefix, n_scen, b);
         dq[q] = descs + s;
         lb[q] = b - __ldg(agent_prefix + s);
+        tq[q] = dq[q]->step;
         const uint32_t a = lb[q] * kAgentBlock + threadIdx.x;
-        live[q] = dq[q]->step < dq[q]->end_step && a < 2u * dq[q]->n_per_side;
+        live[q] = tq[q] < dq[q]->end_step && a < 2u * dq[q]->n_per_side;
         if (live[q]) resolve_load_own(*dq[q], a, r[q]);
         if (live[q] && r[q].code == 0) live[q] = false;
     }
+    // Every thread of the CTA has read its step index: the CTA takes its
+    // ticket now (the reply is needed only at the end).  The CTA holding the
+    // last ticket advances the step index of every scenario of the work list
+    // (clamped at its end) after its own work: by then every CTA has read it.
+    __syncthreads();
+    unsigned int ticket = 0;
+    if (threadIdx.x == 0) ticket = atomicAdd(&ctl->ticket, 1u);
 #pragma unroll
     for (int q = 0; q < kResolveBlocks; ++q)
-        if (live[q]) resolve_load_target(*dq[q], dq[q]->step, r[q]);
+        if (live[q]) resolve_load_target(*dq[q], tq[q], r[q]);
 #pragma unroll
     for (int q = 0; q < kResolveBlocks; ++q) {
         Counts cnt;
-        if (live[q]) resolve_apply(*dq[q], dq[q]->step, r[q], cnt);
+        if (live[q]) resolve_apply(*dq[q], tq[q], r[q], cnt);
         if (blockIdx.x * kResolveBlocks + q < agent_blocks)
             flush_counts(*dq[q], cnt, lb[q] % dq[q]->n_slots);
     }
-    finish_step(descs, n_scen, ctl);
+    if (threadIdx.x < 32) {
+        const bool last = __shfl_sync(0xffffffffu, ticket == gridDim.x - 1, 0);
+        if (last) {
+            ScenarioDesc *md = const_cast<ScenarioDesc *>(descs);
+            for (int i = threadIdx.x; i < n_scen; i += 32) {
+                const unsigned long long v = md[i].step;
+                if (v < md[i].end_step) md[i].step = v + 1;
+            }
+            if (threadIdx.x == 0) ctl->ticket = 0u;
+        }
+    }
 }
+
 
 __global__ void build_pos_kernel(const ScenarioDesc *__restrict__ dp, int plane)
 {
