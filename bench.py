@@ -54,9 +54,18 @@ KERNEL_SOURCES = ["paper_1412_4933_gb300/csrc/pedsim_agent.cu",
                   "paper_1412_4933_gb300/csrc/pedsim_rules.cuh",
                   "paper_1412_4933_gb300/csrc/pedsim_ptx.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "agent_step_aco_2048x2048_traffic.md")
-# kernels of one step of the default (agent-parallel) variant: proposals and
-# stream in one kernel, then resolution (which also advances the step index)
-KERNELS_PER_STEP_CALL = 2
+# Step variants selectable for the headline (the library default is agent),
+# their kernels, and the kernels one sim_step(1) call launches: agent:
+# proposals + stream, then resolution (which also advances the step index);
+# tiled: proposals, resolution, step index; fused: one kernel + step index;
+# two-pass: two kernels + step index.
+VARIANTS = {"agent": lambda P: P.VARIANT_AGENT, "tiled": lambda P: P.VARIANT_TILED,
+            "fused": lambda P: P.VARIANT_FUSED, "two_pass": lambda P: P.VARIANT_TWO_PASS}
+KERNEL_NAMES = {"agent": "agent_stage1_kernel + agent_resolve_kernel",
+                "tiled": "propose_tile_kernel<16> + resolve_tile_kernel<16>",
+                "fused": "fused_step_kernel<64,16>",
+                "two_pass": "propose_plane_kernel + resolve_plane_kernel"}
+KERNELS_PER_STEP_CALL = {"agent": 2, "tiled": 3, "fused": 2, "two_pass": 3}
 
 
 def kernel_source_hash() -> str:
@@ -382,8 +391,10 @@ def run_gpu(args, sc):
         with torch.cuda.stream(stream):
             flush_buf.fill_(1.0)
 
+    variant = VARIANTS[args.variant](P)
     with torch.cuda.stream(stream):
         sim = P.Sim(sc.W, sc.H, P.params_of(sc), stream=stream)
+        sim.set_variant(variant)
         sim.place(sc.seed)
         sim.step(args.warmup)
     torch.cuda.synchronize()
@@ -410,9 +421,10 @@ def run_gpu(args, sc):
     step_s = elapsed / args.steps
     achieved = algo_bytes / step_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": recorded_traffic(),
+                "frac": achieved / peak,
+                "traffic": recorded_traffic() if args.variant == "agent" else None,
                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes,
-                "kernel": "agent_stage1_kernel + agent_resolve_kernel"}
+                "kernel": KERNEL_NAMES[args.variant]}
 
     extra = {}
     if rank == 0 and not args.quick:
@@ -471,7 +483,7 @@ def run_gpu(args, sc):
                              "another buffer)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "clocks": clocks, "gpu_launches": KERNELS_PER_STEP_CALL * args.steps,
+            "clocks": clocks, "gpu_launches": KERNELS_PER_STEP_CALL[args.variant] * args.steps,
             "device_status": status,
         }
         line.update(extra)
@@ -488,6 +500,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WL.ACO_2048.name, choices=sorted(WL.SINGLE))
+    ap.add_argument("--variant", default="agent", choices=sorted(VARIANTS),
+                    help="step variant of the headline simulation")
     ap.add_argument("--steady-steps", type=int, default=2000)
     ap.add_argument("--cpu-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
