@@ -119,8 +119,12 @@ enum { kGridCounts = 4 };
 enum { kVariantPipeline = 0, kVariantTwoPass = 1, kVariantFused = 2, kVariantAgent = 3 };
 
 // Work units of the agent-parallel variant: cells per CTA of its streaming
-// pass, agents per CTA of its proposal and resolution passes.
-constexpr int kCellBlock = 4096;
+// pass (8 per thread: measured best among 4, 8, 16 and 32 at 2048^2 and
+// 8192^2), agents per CTA of its proposal and resolution passes.
+#ifndef PEDSIM_CELL_BLOCK
+#define PEDSIM_CELL_BLOCK 2048
+#endif
+constexpr int kCellBlock = PEDSIM_CELL_BLOCK;
 constexpr int kAgentBlock = 256;
 
 // Supported fused tile shapes (tile_w x tile_h).

@@ -346,11 +346,6 @@ __device__ __forceinline__ int scenario_of(const uint32_t *__restrict__ prefix, 
     return lo;
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
 // Barrier 1 over the consumer warps only (the producer warp never joins).
 __device__ __forceinline__ void consumer_sync()
 {

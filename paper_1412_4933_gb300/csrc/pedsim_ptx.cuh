@@ -87,6 +87,22 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int 
         : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Untiled bulk copy global -> shared (cp.async.bulk): both addresses 16-byte
+// aligned, size a multiple of 16 bytes; completes `bytes` of transaction
+// count on `bar`.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 
 // Waits until every committed bulk store has finished reading shared memory.
@@ -131,13 +147,13 @@ __device__ __forceinline__ void flush_counts(const ScenarioDesc &d, Counts &c, u
 // Launch that may overlap the previous kernel in the stream (programmatic
 // dependent launch); the kernel orders itself with pdl_wait.
 template <class... KArgs, class... Args>
-static cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block,
-                              cudaStream_t stream, Args... args)
+static cudaError_t launch_pdl_smem(void (*kernel)(KArgs...), unsigned grid, unsigned block,
+                                   unsigned smem, cudaStream_t stream, Args... args)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -145,6 +161,13 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+template <class... KArgs, class... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block,
+                              cudaStream_t stream, Args... args)
+{
+    return launch_pdl_smem(kernel, grid, block, 0u, stream, args...);
 }
 
 }  // namespace pedsim
