@@ -129,78 +129,6 @@ __device__ __forceinline__ void stream_block(const ScenarioDesc *__restrict__ de
     }
 }
 
-#ifdef PEDSIM_STAGE1_BULK
-// CTA i evaporates cell block i (if any) and proposes agent block i (if
-// any).  Thread 0 starts untiled bulk copies of the block's two pheromone
-// planes into shared memory; the proposals run while they are in flight;
-// then every thread evaporates its share from shared memory to the planes of
-// t+1.  Registers hold no streamed data, so the copies of all resident CTAs
-// (2 x kCellBlock x 4 bytes each) are in flight together.
-constexpr size_t kStage1Smem = 2 * (size_t)kCellBlock * 4 + 16 + 128;
-
-__global__ void __launch_bounds__(kAgentBlock)
-agent_stage1_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__restrict__ cell_prefix,
-                    const uint32_t *__restrict__ agent_prefix, int n_scen, uint32_t cell_blocks,
-                    uint32_t agent_blocks)
-{
-    extern __shared__ __align__(128) uint8_t smem_raw[];
-    uint8_t *const smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    float *const plane_s = reinterpret_cast<float *>(smem);  // [2][kCellBlock]
-    uint64_t *const bar = reinterpret_cast<uint64_t *>(smem + 2 * (size_t)kCellBlock * 4);
-    // The state at t is the previous step's output: wait for it, then let
-    // the resolution kernel be scheduled (it waits for this one).
-    pdl_wait();
-    pdl_trigger();
-    const uint32_t i = blockIdx.x;
-    const ScenarioDesc *ds = nullptr;
-    size_t c0 = 0;
-    uint32_t n = 0;
-    int p = 0;
-    if (i < cell_blocks) {
-        const int s = block_scenario(cell_prefix, n_scen, i);
-        ds = descs + s;
-        if (ds->step < ds->end_step) {
-            const size_t cells = (size_t)ds->W * (size_t)ds->H;
-            c0 = (size_t)(i - __ldg(cell_prefix + s)) * kCellBlock;
-            n = (uint32_t)(cells - c0 < (size_t)kCellBlock ? cells - c0 : kCellBlock);
-            p = (int)(ds->step & 1);
-        }
-        if (threadIdx.x == 0 && n) {
-            mbar_init(bar, 1);
-            fence_mbarrier_init();
-            mbar_arrive_expect_tx(bar, 2 * n * 4);
-            bulk_load(plane_s, ds->tau[0][p] + c0, n * 4, bar);
-            bulk_load(plane_s + kCellBlock, ds->tau[1][p] + c0, n * 4, bar);
-        }
-    }
-    if (i < agent_blocks) {
-        const int s = block_scenario(agent_prefix, n_scen, i);
-        const ScenarioDesc &d = descs[s];
-        const uint64_t t = d.step;
-        const uint32_t a = (i - __ldg(agent_prefix + s)) * kAgentBlock + threadIdx.x;
-        if (t < d.end_step && a < 2u * d.n_per_side) propose_agent(d, a, t);
-    }
-    if (!n) return;  // uniform over the CTA
-    bool ok = true;
-    if (threadIdx.x == 0) ok = mbar_wait_bounded(bar, 0);
-    if (!__syncthreads_and(ok)) {
-        if (threadIdx.x == 0) atomicExch(ds->error, kErrTimeout);
-        return;
-    }
-    const float q = ds->q;
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-        const float4 *src = reinterpret_cast<const float4 *>(plane_s + g * kCellBlock);
-        float4 *dst = reinterpret_cast<float4 *>(ds->tau[g][p ^ 1] + c0);
-#pragma unroll 4
-        for (uint32_t k = threadIdx.x; k < n / 4; k += kAgentBlock) {
-            const float4 a4 = src[k];
-            dst[k] = make_float4(__fmul_rn(a4.x, q), __fmul_rn(a4.y, q), __fmul_rn(a4.z, q),
-                                 __fmul_rn(a4.w, q));
-        }
-    }
-}
-#else
 
 __global__ void __launch_bounds__(kAgentBlock)
 agent_stage1_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__restrict__ cell_prefix,
@@ -229,7 +157,6 @@ agent_stage1_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__re
         if (t < d.end_step && a < 2u * d.n_per_side) propose_agent(d, a, t);
     }
 }
-#endif
 
 // Resolution work of one agent: its own entries (first round of loads) and
 // its target's neighbourhood (second round).  Nothing read here is written
@@ -393,22 +320,10 @@ cudaError_t launch_agent_step(const ScenarioDesc *d_descs, const uint32_t *d_cel
 {
     if (n <= 0) return cudaSuccess;
     if (cell_blocks + agent_blocks) {
-#ifdef PEDSIM_STAGE1_BULK
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(agent_stage1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kStage1Smem);
-            attr = true;
-        }
-        const uint32_t grid1 = cell_blocks > agent_blocks ? cell_blocks : agent_blocks;
-        cudaError_t e = launch_pdl_smem(agent_stage1_kernel, grid1, (unsigned)kAgentBlock,
-                                        (unsigned)kStage1Smem, stream, d_descs, d_cell_prefix,
-                                        d_agent_prefix, n, cell_blocks, agent_blocks);
-#else
         cudaError_t e = launch_pdl(agent_stage1_kernel, cell_blocks + agent_blocks,
                                    (unsigned)kAgentBlock, stream, d_descs, d_cell_prefix,
                                    d_agent_prefix, n, cell_blocks, agent_blocks);
-#endif
+
         if (e != cudaSuccess) return e;
     }
     // the resolution kernel also advances the step index: with no agent it
