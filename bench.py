@@ -53,6 +53,7 @@ sys.path.insert(0, ROOT)
 from paper_1412_4933_gb300 import workloads as WL  # noqa: E402
 
 L2_FLUSH_BYTES = 512 << 20
+NOMINAL_HBM_GBPS = 7900.0  # GB300 HBM3e nominal, for context beside the measured peak
 ALGO_BYTES_PER_CELL = {WL.LEM: 2, WL.ACO: 18}
 KERNEL_SOURCES = ["paper_1412_4933_gb300/csrc/pedsim_agent.cu",
                   "paper_1412_4933_gb300/csrc/pedsim_rules.cuh",
@@ -200,6 +201,27 @@ def oracle_rate(sc, steps: int, warm: int = 0):
     orc.step(steps)
     dt = time.perf_counter() - t0
     return sc.cells * steps / dt, dt
+
+
+def oracle_multicore(scs, steps: int, cores: int):
+    """The oracle on `cores` host cores at once, one scenario per core (the
+    first `cores` scenarios), `steps` steps each, in spawned processes:
+    aggregate cell-updates/s over the wall time of the parallel run."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from oracle import oracle as O
+    O.build()
+    jobs = scs[:cores]
+    with cf.ProcessPoolExecutor(max_workers=len(jobs), mp_context=mp.get_context("spawn")) as ex:
+        futs = [ex.submit(O.timed_run, sc.W, sc.H, sc.params(), sc.seed, steps) for sc in jobs]
+        res = [f.result(timeout=600) for f in futs]
+    # the workers step at the same time, each timing its own steps (process
+    # start-up and placement excluded): total work over the longest run
+    work = sum(r[0] for r in res)
+    longest = max(r[1] for r in res)
+    return {"value": work / longest, "unit": "cell-updates/s", "cores": len(jobs), "kind": "oracle",
+            "sample": f"{steps} steps of each of the first {len(jobs)} batch scenarios, one per "
+                      f"core in parallel (longest {longest:.2f} s)"}
 
 
 def run_reference(args, sc):
@@ -375,7 +397,9 @@ def batched_leg(P, torch, stream, count=256, steps=500):
     for sim in sims:
         sim.close()
     single_rate = sum(s.cells for s in sample) * (steps // 10) / t_single
+    cpu = oracle_multicore(scs, steps=50, cores=min(16, os.cpu_count() or 1))
     return {"scenarios": count, "steps": steps, "cells": cells,
+            "cpu_oracle_multicore": cpu,
             "launch_config": {"variant": choice[0], "tile": [choice[1], choice[2]],
                               "ctas_per_sm": choice[3]},
             "scenarios_per_s": count / t_batch,
@@ -450,6 +474,7 @@ def run_gpu(args, sc):
     step_s = elapsed / args.steps
     achieved = algo_bytes / step_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac_of_nominal": achieved / NOMINAL_HBM_GBPS, "nominal_peak": NOMINAL_HBM_GBPS,
                 "frac": achieved / peak,
                 "traffic": recorded_traffic() if args.variant == "agent" else None,
                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes,

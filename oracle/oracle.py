@@ -171,3 +171,14 @@ class Oracle:
 
     def decide_at(self, x: int, y: int) -> int:
         return int(lib().orc_decide_at(self._h, x, y))
+
+
+def timed_run(W: int, H: int, params: dict, seed: int, steps: int):
+    """Places a scenario and times `steps` oracle steps; returns
+    (W * H * steps, seconds).  Module-level so that a spawned process pool
+    can run it (benchmark use: the oracle on several host cores at once)."""
+    orc = Oracle(W, H, make_params(**params), seed)
+    import time
+    t0 = time.perf_counter()
+    orc.step(steps)
+    return W * H * steps, time.perf_counter() - t0
