@@ -366,7 +366,7 @@ def batched_leg(P, torch, stream, count=256, steps=500):
     from paper_1412_4933_gb300 import autotune
     scs = WL.batched_scenarios(count=count, steps=steps)
     cells = sum(s.cells for s in scs)
-    choice = autotune.tune(scs, steps=16, stream=stream)
+    choice = autotune.tune(scs, stream=stream)
     batch = P.Batch(scs, stream=stream)
     autotune.apply(batch, choice)
     batch.step(16)

@@ -73,9 +73,11 @@ def apply(batch, choice) -> None:
         batch.set_tiling(tw, th, cps)
 
 
-def tune(scenarios, steps: int = 16, candidates=CANDIDATES, use_cache: bool = True,
-         stream=None) -> tuple:
-    """Best (variant, tile_w, tile_h, ctas_per_sm) for this batch of scenarios."""
+def tune(scenarios, steps: int = 32, candidates=CANDIDATES, use_cache: bool = True,
+         stream=None, repeats: int = 2) -> tuple:
+    """Best (variant, tile_w, tile_h, ctas_per_sm) for this batch of scenarios:
+    each candidate runs 16 warm-up steps (graph capture), then is timed over
+    `steps` steps `repeats` times; the best of its repeats counts."""
     import torch
     key = f"{_gpu_name()}|{size_class(scenarios)}"
     cache = _load_cache() if use_cache else {}
@@ -86,12 +88,15 @@ def tune(scenarios, steps: int = 16, candidates=CANDIDATES, use_cache: bool = Tr
     try:
         for cand in candidates:
             apply(scratch, cand)
-            scratch.step(steps)  # warm-up (graph capture)
+            scratch.step(16)  # warm-up (graph capture)
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            scratch.step(steps)
-            torch.cuda.synchronize()
-            timings.append((time.perf_counter() - t0, cand))
+            best = float("inf")
+            for _ in range(repeats):
+                t0 = time.perf_counter()
+                scratch.step(steps)
+                torch.cuda.synchronize()
+                best = min(best, time.perf_counter() - t0)
+            timings.append((best, cand))
     finally:
         scratch.close()
     best = min(timings)[1]

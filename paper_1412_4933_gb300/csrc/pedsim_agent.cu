@@ -2,7 +2,7 @@
 // automaton (sm_103a).  One synchronous step (Sec. IV.b-d) is split by
 // access pattern instead of by tile, in two kernels:
 //
-//   agent_stage1_kernel   two CTA roles, interleaved over the grid:
+//   agent_stage1_kernel   two CTA roles, the proposal blocks first:
 //     proposal blocks     one thread per agent: forward first, else the full
 //                         rule (Eq. 1 LEM rank draw, Eq. 2 ACO roulette) from
 //                         the occupancy and pheromone at t; the direction code
@@ -139,17 +139,15 @@ agent_stage1_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__re
     // the resolution kernel be scheduled (it waits for this one).
     pdl_wait();
     pdl_trigger();
-    // CTA i is a proposal block when the count floor((i + 1) A / T) of
-    // proposal blocks among CTAs 0..i grows at i (A proposal blocks spread
-    // evenly over all T CTAs), else a stream block.
-    const uint64_t total = (uint64_t)cell_blocks + agent_blocks;
+    // CTAs 0 .. A-1 are the proposal blocks, the rest the stream blocks:
+    // proposal CTAs (latency chains, longer in congestion) start in the
+    // first wave and end before the stream's tail; measured faster than
+    // spreading them evenly over the grid, in free flow and in gridlock.
     const uint32_t i = blockIdx.x;
-    const uint32_t na = (uint32_t)(((uint64_t)(i + 1) * agent_blocks) / total);
-    const uint32_t na_before = (uint32_t)(((uint64_t)i * agent_blocks) / total);
-    if (na == na_before) {
-        stream_block(descs, cell_prefix, n_scen, i - na);
+    if (i >= agent_blocks) {
+        stream_block(descs, cell_prefix, n_scen, i - agent_blocks);
     } else {
-        const uint32_t b = na - 1;
+        const uint32_t b = i;
         const int s = block_scenario(agent_prefix, n_scen, b);
         const ScenarioDesc &d = descs[s];
         const uint64_t t = d.step;
@@ -233,11 +231,9 @@ __device__ __forceinline__ void resolve_apply(const ScenarioDesc &d, uint64_t t,
 }
 
 // Each CTA resolves kResolveBlocks consecutive agent blocks, one agent of
-// each per thread, with the loads of all of them in flight together.
-#ifndef PEDSIM_RESOLVE_BLOCKS
-#define PEDSIM_RESOLVE_BLOCKS 1
-#endif
-constexpr int kResolveBlocks = PEDSIM_RESOLVE_BLOCKS;
+// each per thread, with the loads of all of them in flight together (1: 2
+// and 4 were measured slower at 2048^2 and 8192^2).
+constexpr int kResolveBlocks = 1;
 
 __global__ void __launch_bounds__(kAgentBlock)
 agent_resolve_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__restrict__ agent_prefix,

@@ -99,7 +99,7 @@ def run(scenarios, stream=None, variant=None, tune: bool = True):
         if variant is not None:
             b.set_variant(variant)
         elif tune:
-            autotune.apply(b, autotune.tune(scenarios, steps=16, stream=stream))
+            autotune.apply(b, autotune.tune(scenarios, stream=stream))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         b.step(steps)
