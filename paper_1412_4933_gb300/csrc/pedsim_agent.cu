@@ -133,21 +133,46 @@ __device__ __forceinline__ void stream_block(const ScenarioDesc *__restrict__ de
 __global__ void __launch_bounds__(kAgentBlock)
 agent_stage1_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__restrict__ cell_prefix,
                     const uint32_t *__restrict__ agent_prefix, int n_scen, uint32_t cell_blocks,
-                    uint32_t agent_blocks)
+                    uint32_t agent_blocks, uint32_t front)
 {
     // The state at t is the previous step's output: wait for it, then let
     // the resolution kernel be scheduled (it waits for this one).
     pdl_wait();
     pdl_trigger();
-    // CTAs 0 .. A-1 are the proposal blocks, the rest the stream blocks:
-    // proposal CTAs (latency chains, longer in congestion) start in the
-    // first wave and end before the stream's tail; measured faster than
-    // spreading them evenly over the grid, in free flow and in gridlock.
+    // CTAs 0 .. front-1 are the first proposal blocks (at most one resident
+    // wave): proposal CTAs (latency chains, longer in congestion) start at
+    // once and end before the stream's tail, which measured faster than an
+    // even spread when all proposals fit in that wave.  The remaining R
+    // proposal blocks are spread evenly over the remaining T CTAs (CTA
+    // front + j holds one where floor(j R / T) steps up), so that on large
+    // grids the stream does not wait behind waves of proposals.
     const uint32_t i = blockIdx.x;
-    if (i >= agent_blocks) {
-        stream_block(descs, cell_prefix, n_scen, i - agent_blocks);
+    uint32_t b = i;   // proposal block of this CTA, or agent_blocks
+    uint32_t sb = 0;  // stream block of this CTA otherwise
+    if (i >= front) {
+        const uint32_t j = i - front;
+        const uint32_t rest = agent_blocks - front;
+        if (rest == 0) {
+            b = agent_blocks;
+            sb = j;
+        } else {
+            const uint32_t ctas = cell_blocks + rest;
+            const uint64_t lo = (uint64_t)j * rest, hi = lo + rest;
+            // 32-bit divisions whenever the products fit (all single grids
+            // up to 2^31 cells), 64-bit ones otherwise
+            const uint32_t before = hi >> 32 ? (uint32_t)(lo / ctas) : (uint32_t)lo / ctas;
+            const uint32_t after = hi >> 32 ? (uint32_t)(hi / ctas) : (uint32_t)hi / ctas;
+            if (after > before) {
+                b = front + before;
+            } else {
+                b = agent_blocks;
+                sb = j - before;
+            }
+        }
+    }
+    if (b >= agent_blocks) {
+        stream_block(descs, cell_prefix, n_scen, sb);
     } else {
-        const uint32_t b = i;
         const int s = block_scenario(agent_prefix, n_scen, b);
         const ScenarioDesc &d = descs[s];
         const uint64_t t = d.step;
@@ -316,9 +341,20 @@ cudaError_t launch_agent_step(const ScenarioDesc *d_descs, const uint32_t *d_cel
 {
     if (n <= 0) return cudaSuccess;
     if (cell_blocks + agent_blocks) {
+        // one resident wave of the first kernel (occupancy queried once)
+        static uint32_t wave = 0;
+        if (!wave) {
+            int dev = 0, sms = 0, per_sm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, agent_stage1_kernel,
+                                                          kAgentBlock, 0);
+            wave = (uint32_t)(sms > 0 ? sms : 1) * (uint32_t)(per_sm > 0 ? per_sm : 1);
+        }
+        const uint32_t front = agent_blocks < wave ? agent_blocks : wave;
         cudaError_t e = launch_pdl(agent_stage1_kernel, cell_blocks + agent_blocks,
                                    (unsigned)kAgentBlock, stream, d_descs, d_cell_prefix,
-                                   d_agent_prefix, n, cell_blocks, agent_blocks);
+                                   d_agent_prefix, n, cell_blocks, agent_blocks, front);
 
         if (e != cudaSuccess) return e;
     }
