@@ -70,7 +70,6 @@ KERNEL_NAMES = {"agent": "agent_stage1_kernel + agent_resolve_kernel",
                 "tiled": "propose_tile_kernel<16> + resolve_tile_kernel<16>",
                 "fused": "fused_step_kernel<64,16>",
                 "two_pass": "propose_plane_kernel + resolve_plane_kernel"}
-KERNELS_PER_STEP_CALL = {"agent": 2, "tiled": 3, "fused": 2, "two_pass": 3}
 
 
 def kernel_source_hash() -> str:
@@ -460,6 +459,7 @@ def run_gpu(args, sc):
     elapsed_max = max_over_ranks(elapsed, dist, device)
     clocks = clk.summary()
     status = sim.device_status()
+    launches = sim.launches_per_step()
 
     cells_total = sc.cells * args.steps * world
     value = cells_total / elapsed_max
@@ -538,7 +538,7 @@ def run_gpu(args, sc):
                              "another buffer)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "clocks": clocks, "gpu_launches": KERNELS_PER_STEP_CALL[args.variant] * args.steps,
+            "clocks": clocks, "gpu_launches": launches * args.steps,
             "device_status": status,
         }
         line.update(extra)

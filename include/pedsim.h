@@ -173,11 +173,12 @@ int sim_load(sim_t *s, const void *buf, size_t len);
  *                         the halo instead of a proposal plane); only tiles
  *                         with an agent in or next to them take the full
  *                         rule, the others only evaporate
- * PEDSIM_VARIANT_AGENT    (default) three kernels per step: one thread per agent
- *                         computes its proposal while every cell's pheromone
- *                         evaporates in a separate streaming pass; then one
- *                         thread per agent resolves its target cell and
- *                         applies the winner's move and deposit
+ * PEDSIM_VARIANT_AGENT    (default) two kernels per step: one thread per agent
+ *                         computes its proposal while the other CTAs of the
+ *                         same kernel stream every cell's pheromone
+ *                         evaporation; then one thread per agent resolves its
+ *                         target cell, applies the winner's move and deposit
+ *                         and the last CTA advances the step index
  * Selecting a variant resets the tile shape to its default (tiled: 128 x 16;
  * fused: 64 x 16; the agent variant has none).                                */
 #define PEDSIM_VARIANT_TILED    0
@@ -185,6 +186,11 @@ int sim_load(sim_t *s, const void *buf, size_t len);
 #define PEDSIM_VARIANT_FUSED    2
 #define PEDSIM_VARIANT_AGENT    3
 int sim_set_variant(sim_t *s, int variant);
+
+/* Kernel launches that sim_step(s, 1) issues with the current variant into
+ * *out (agent: 2; fused: 2; tiled and two-pass: 3, each counting the
+ * step-index advance); PEDSIM_EINVAL for a null argument.                     */
+int sim_launches_per_step(sim_t *s, int *out);
 
 /* Tile shape of the current variant: tiled: tile_w = 128, tile_h in
  * {8, 16}; fused: (tile_w, tile_h) in {(32,16), (64,8), (64,16),

@@ -780,6 +780,18 @@ int sim_set_tiling(sim_t *s, int tile_w, int tile_h, int ctas_per_sm)
     return upload_desc(s);
 }
 
+int sim_launches_per_step(sim_t *s, int *out)
+{
+    if (!s || !out) return fail(s, PEDSIM_EINVAL, "null argument");
+    if (s->variant == kVariantAgent)
+        *out = 2;  // proposals and stream, then the resolution (it advances the step)
+    else if (s->variant == kVariantFused)
+        *out = 2;  // the step and the step-index advance
+    else
+        *out = 3;  // proposals, resolution and the step-index advance
+    return PEDSIM_OK;
+}
+
 int sim_device_status(sim_t *s)
 {
     if (!s) return PEDSIM_EINVAL;

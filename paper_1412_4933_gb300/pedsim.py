@@ -63,6 +63,7 @@ _SIGS = {
     "sim_set_variant": (C.c_int, [_P, C.c_int]),
     "sim_set_tiling": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
     "sim_device_status": (C.c_int, [_P]),
+    "sim_launches_per_step": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "sim_destroy": (None, [_P]),
     "sim_last_error": (C.c_char_p, [_P]),
     "sim_batch_create": (C.c_int, [C.c_int, _P, _P, _P, _P, C.POINTER(_P)]),
@@ -220,6 +221,12 @@ class Sim:
 
     def device_status(self) -> int:
         return int(_lib.sim_device_status(self._h))
+
+    def launches_per_step(self) -> int:
+        """Kernel launches of one step(1) call with the current variant."""
+        n = C.c_int(0)
+        self._check(_lib.sim_launches_per_step(self._h, C.byref(n)))
+        return int(n.value)
 
     def close(self) -> None:
         h = getattr(self, "_h", None)

@@ -221,6 +221,19 @@ def test_checkpoint_resume_bit_exact(sc, variant):
     assert a.stats() == b.stats() == orc.stats()
 
 
+def test_launches_per_step_query():
+    """sim_launches_per_step reports each variant's kernels of one step."""
+    sc = SMALL[1]
+    sim = P.Sim(sc.W, sc.H, P.params_of(sc))
+    try:
+        for v, n in ((P.VARIANT_AGENT, 2), (P.VARIANT_FUSED, 2), (P.VARIANT_TILED, 3),
+                     (P.VARIANT_TWO_PASS, 3)):
+            sim.set_variant(v)
+            assert sim.launches_per_step() == n
+    finally:
+        sim.close()
+
+
 def test_runs_on_a_side_stream():
     sc = SMALL[1]
     s = torch.cuda.Stream()
