@@ -4,13 +4,23 @@ Headline (one JSON line on rank 0): cell-updates/s of the ACO step on the
 2048x2048 grid with 100K agents (50K per side in 64-column bands, rho 0.02),
 one "step" = one synchronous automaton step (proposal, gather resolution,
 move, evaporation + deposit, counters) over the whole grid, inputs resident
-in HBM.  L2 is flushed between timed steps because the scenario's working
-set (~92 MB) would otherwise stay in the 129 MB L2: a 512 MB write, then a
-256 MB read of another buffer, so that the write-backs of the flush's own
-dirty lines happen before the step rather than inside it (the write-only
-flush is reported beside it as `flushed_write_only`).
+in HBM.  One scenario's working set (~92 MB) would stay in the 129 MB L2,
+so the timed steps take inputs larger than L2: four resident instances of
+the workload (seeds 3..6) are stepped in turn, one single-scenario step
+each (CUDA graphs of four rounds, replayed), so every step reads its state
+from HBM and the write-backs of earlier steps land inside the timed region;
+one event pair around all K steps.
 
 Also reported on the same line:
+  flushed_per_step
+                the same single-scenario step with the L2 flushed before
+                each step (a 512 MB write, then a 256 MB read of another
+                buffer, so the flush's own write-backs happen before the
+                step) and an event pair around each step: every step then
+                also starts with cold instruction and descriptor caches
+  flushed_write_only
+                the same with the write-only flush (its write-backs land
+                in the step)
   roofline      the step's kernels (proposals + stream, resolution):
                 algorithmic bytes (18 B/cell) / step time vs the measured HBM
                 copy bandwidth
@@ -53,6 +63,7 @@ sys.path.insert(0, ROOT)
 from paper_1412_4933_gb300 import workloads as WL  # noqa: E402
 
 L2_FLUSH_BYTES = 512 << 20
+ROTATING_INSTANCES = 4  # headline: 4 x ~95 MB of state, well above the 129 MB L2
 NOMINAL_HBM_GBPS = 7900.0  # GB300 HBM3e nominal, for context beside the measured peak
 ALGO_BYTES_PER_CELL = {WL.LEM: 2, WL.ACO: 18}
 KERNEL_SOURCES = ["paper_1412_4933_gb300/csrc/pedsim_agent.cu",
@@ -254,6 +265,62 @@ def run_reference(args, sc):
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
+def rotating_instances(P, torch, sc, stream, variant, warmup: int, count: int):
+    """`count` resident instances of the workload (seeds sc.seed + k), each
+    placed and advanced `warmup` steps."""
+    sims = []
+    with torch.cuda.stream(stream):
+        for k in range(count):
+            s = P.Sim(sc.W, sc.H, P.params_of(sc), stream=stream)
+            s.set_variant(variant)
+            s.place(sc.seed + k)
+            s.step(warmup)
+            sims.append(s)
+    torch.cuda.synchronize()
+    return sims
+
+
+ROUNDS_PER_GRAPH = 4  # rounds of one step per instance in one graph replay
+
+
+def capture_rounds(sims, torch, stream, rounds: int):
+    """`rounds` rounds of one step of every instance in turn, captured as one
+    CUDA graph (the library's launches go into the capturing stream; kernels
+    of consecutive steps overlap by programmatic dependent launch only
+    inside a graph) and replayed once."""
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        for _ in range(rounds):
+            for s in sims:
+                s.step(1)
+    with torch.cuda.stream(stream):
+        g.replay()
+    torch.cuda.synchronize()
+    return g
+
+
+def time_steps_rotating(sims, graphs, torch, stream, steps: int) -> float:
+    """Seconds for `steps` single-scenario steps, step i advancing instance
+    i % len(sims) (replays of the ROUNDS_PER_GRAPH-round graph, then of the
+    one-round graph, then single steps), with one event pair around all of
+    them."""
+    big, one = graphs
+    rounds, rem = divmod(steps, len(sims))
+    n_big, n_one = divmod(rounds, ROUNDS_PER_GRAPH)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(n_big):
+            big.replay()
+        for _ in range(n_one):
+            one.replay()
+        for s in sims[:rem]:
+            s.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e-3
+
+
 def time_steps_flushed(sim, torch, stream, steps: int, flush):
     """Sum of per-step CUDA-event times; L2 flushed between steps (outside
     the events)."""
@@ -444,31 +511,37 @@ def run_gpu(args, sc):
             flush_buf.fill_(1.0)
 
     variant = VARIANTS[args.variant](P)
-    with torch.cuda.stream(stream):
-        sim = P.Sim(sc.W, sc.H, P.params_of(sc), stream=stream)
-        sim.set_variant(variant)
-        sim.place(sc.seed)
-        sim.step(args.warmup)
-    torch.cuda.synchronize()
+    # inputs larger than L2: ROTATING_INSTANCES resident copies of the
+    # workload, stepped in turn, so that every step reads its state from HBM
+    sims = rotating_instances(P, torch, sc, stream, variant, args.warmup, ROTATING_INSTANCES)
+    sim = sims[0]
+    graphs = (capture_rounds(sims, torch, stream, ROUNDS_PER_GRAPH),
+              capture_rounds(sims, torch, stream, 1))
     barrier(dist, device)
 
     with ClockSampler(local) as clk:
-        per_step = time_steps_flushed(sim, torch, stream, args.steps, flush)
+        elapsed = time_steps_rotating(sims, graphs, torch, stream, args.steps)
     barrier(dist, device)
-    elapsed = sum(per_step)
     elapsed_max = max_over_ranks(elapsed, dist, device)
     clocks = clk.summary()
-    status = sim.device_status()
+    status = max(abs(x.device_status()) for x in sims)
     launches = sim.launches_per_step()
+    del graphs
+    for x in sims[1:]:
+        x.close()
+    # the same single-scenario step with the L2 flushed before each step and
+    # an event pair around each step
+    per_step = time_steps_flushed(sim, torch, stream, args.steps, flush)
+    fl_s = sum(per_step) / len(per_step)
 
     cells_total = sc.cells * args.steps * world
     value = cells_total / elapsed_max
     ms_per_step = elapsed_max * 1e3 / args.steps
 
     # roofline of the step: algorithmic bytes / time.  The per-step time holds
-    # all of the step's kernels (the first kernel streams the bytes with the
-    # proposals interleaved; the resolution kernel and the step-index kernel
-    # follow it), so this is a lower bound of the streaming part's rate
+    # both of the step's kernels (the first streams the bytes with the
+    # proposals interleaved, the resolution follows it), so this is a lower
+    # bound of the streaming part's rate
     algo_bytes = ALGO_BYTES_PER_CELL[sc.model] * sc.cells
     peak, peak_kind = measured_peak()
     step_s = elapsed / args.steps
@@ -480,7 +553,11 @@ def run_gpu(args, sc):
                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes,
                 "kernel": KERNEL_NAMES[args.variant]}
 
-    extra = {}
+    extra = {"flushed_per_step": {
+        "steps": len(per_step), "us_per_step": fl_s * 1e6, "cell_updates_per_s": sc.cells / fl_s,
+        "algorithmic_GBps": algo_bytes / fl_s / 1e9, "frac_of_peak": algo_bytes / fl_s / 1e9 / peak,
+        "l2": "flushed before each step (512 MB write, then a 256 MB read of another buffer), "
+              "one event pair per step"}}
     if rank == 0 and not args.quick:
         # the same steps with the write-only flush (its write-backs land in
         # the step)
@@ -534,8 +611,10 @@ def run_gpu(args, sc):
             "config": {"workload": sc.name, "W": sc.W, "H": sc.H, "agents": sc.agents,
                        "model": "ACO" if sc.model else "LEM", "rho": sc.rho, "seed": sc.seed,
                        "band_cols": sc.band_cols,
-                       "l2": "flushed between timed steps (512 MB write, then a 256 MB read of "
-                             "another buffer)",
+                       "l2": f"inputs larger than L2: {ROTATING_INSTANCES} resident instances of "
+                             f"the workload (seeds {sc.seed}..{sc.seed + ROTATING_INSTANCES - 1}, "
+                             f"~95 MB of state each) stepped in turn, one step each, so every "
+                             f"step reads its state from HBM; one event pair around all steps",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks, "gpu_launches": launches * args.steps,
