@@ -131,7 +131,10 @@ int sim_set_stream(sim_t *s, void *stream);
 int sim_place(sim_t *s, uint64_t seed);
 
 /* Advances n >= 0 synchronous steps (Sec. IV.b-d), asynchronously on the
- * stream.  Long runs replay a captured CUDA graph.                            */
+ * stream.  Long runs replay a captured CUDA graph.  A call with n < 16
+ * issues plain kernel launches and may be captured into the caller's own
+ * CUDA graph: every replay advances the step index kept on the device, which
+ * sim_read_grid, sim_stats and sim_save take as the current step.            */
 int sim_step(sim_t *s, int n);
 
 /* Copies the grid at the current step into host buffers (any may be NULL);

@@ -391,6 +391,19 @@ int occ_plane(const sim_t *s, int variant, unsigned long long step)
 }
 int occ_plane(const sim_t *s) { return occ_plane(s, s->variant, s->step); }
 
+// The step index the kernels use lives in the device descriptor; the host
+// copy follows every sim_step call, but a caller that replays a CUDA graph it
+// captured around sim_step advances only the device's.  Read-back calls take
+// the device's value first (it selects the planes that hold the state).
+int resync_step(sim_t *s)
+{
+    unsigned long long dstep = 0;
+    SIM_CUDA(s, cudaMemcpyAsync(&dstep, &s->d_desc->step, 8, cudaMemcpyDeviceToHost, s->stream));
+    SIM_CUDA(s, cudaStreamSynchronize(s->stream));
+    s->step = dstep;
+    return PEDSIM_OK;
+}
+
 // Changes the step variant and tiling of a scenario between steps: the
 // occupancy moves to the plane the new variant keeps it in, and the agent
 // positions are rebuilt when the new variant is the agent-parallel one (only
@@ -539,6 +552,7 @@ int sim_step(sim_t *s, int n)
 int sim_read_grid(sim_t *s, uint8_t *occ, uint32_t *ids, float *tauA, float *tauB)
 {
     if (!s) return PEDSIM_EINVAL;
+    if (int rc = resync_step(s)) return rc;
     const size_t cells = (size_t)s->W * s->H;
     const int par = (int)(s->step & 1);
     const int oplane = occ_plane(s);
@@ -631,6 +645,7 @@ int sim_set_state(sim_t *s, uint64_t seed, uint64_t step, const uint8_t *occ, co
 int sim_stats(sim_t *s, sim_stats_t *out)
 {
     if (!s || !out) return PEDSIM_EINVAL;
+    if (int rc = resync_step(s)) return rc;
     unsigned long long ctr[kNumCounters], dstep = 0;
     unsigned int counts[kGridCounts];
     const int par = occ_plane(s);
@@ -684,6 +699,7 @@ int sim_save(sim_t *s, void *buf, size_t *len)
         return PEDSIM_OK;
     }
     if (*len < need) return fail(s, PEDSIM_EINVAL, "checkpoint buffer too small");
+    if (int rc = resync_step(s)) return rc;
     const size_t cells = (size_t)s->W * s->H, na = agents_len(s);
     CkptHeader h{};
     std::memcpy(h.magic, "PEDSIM01", 8);

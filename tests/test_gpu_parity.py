@@ -246,6 +246,41 @@ def test_runs_on_a_side_stream():
     assert_same(sim, orc, "side stream")
 
 
+def test_instances_in_turn_from_a_captured_graph():
+    """The benchmark's launch configuration: instances stepped in turn, one
+    step each, from a CUDA graph of several rounds captured around the
+    library's launches and replayed; every instance matches the oracle."""
+    scs = [SMALL[1], SMALL[1].with_(seed=SMALL[1].seed + 1), EDGE[4]]
+    s = torch.cuda.Stream()
+    sims = []
+    with torch.cuda.stream(s):
+        for sc in scs:
+            sim = P.Sim(sc.W, sc.H, P.params_of(sc), stream=s)
+            sim.place(sc.seed)
+            sim.step(3)
+            sims.append(sim)
+    g = torch.cuda.CUDAGraph()
+    # the host's copy of the step index counts the captured steps only (3 +
+    # 3): the device's (3 + 12) has the other parity, so a read-back that
+    # trusted the host copy would read the other pheromone plane
+    rounds, replays = 3, 4
+    with torch.cuda.graph(g, stream=s):
+        for _ in range(rounds):
+            for sim in sims:
+                sim.step(1)
+    with torch.cuda.stream(s):
+        for _ in range(replays):
+            g.replay()
+    torch.cuda.synchronize()
+    for sc, sim in zip(scs, sims):
+        orc = O.Oracle(sc.W, sc.H, oparams(sc), sc.seed)
+        orc.step(3 + rounds * replays)
+        assert_same(sim, orc, f"{sc.name} after graph replays", aco=sc.model == WL.ACO)
+        assert sim.stats() == orc.stats()
+        assert sim.device_status() == 0
+        sim.close()
+
+
 @pytest.mark.parametrize("variant", VARIANTS, ids=VARIANT_IDS)
 def test_batch_matches_single_runs(variant):
     scs = WL.batched_scenarios(count=12, steps=40, side_lo=64, side_hi=256)
