@@ -637,7 +637,7 @@ def main():
     ap.add_argument("--variant", default="agent", choices=sorted(VARIANTS),
                     help="step variant of the headline simulation")
     ap.add_argument("--steady-steps", type=int, default=2000)
-    ap.add_argument("--cpu-steps", type=int, default=100)
+    ap.add_argument("--cpu-steps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
