@@ -28,11 +28,15 @@
 // ends, and it waits for the first kernel's completion.  The last CTA of
 // the resolution kernel advances the step index itself, so a step is two
 // launches and a captured graph replays at any step.
+#include <atomic>
+
 #include "pedsim_internal.h"
 #include "pedsim_rules.cuh"
 #include "pedsim_ptx.cuh"
 
 namespace pedsim {
+
+constexpr int kMaxDevices = 64;  // devices whose occupancy is cached
 
 
 // Scenario of work block b (prefix[i] = first block of scenario i).
@@ -344,15 +348,19 @@ cudaError_t launch_agent_step(const ScenarioDesc *d_descs, const uint32_t *d_cel
 {
     if (n <= 0) return cudaSuccess;
     if (cell_blocks + agent_blocks) {
-        // one resident wave of the first kernel (occupancy queried once)
-        static uint32_t wave = 0;
+        // one resident wave of the first kernel (occupancy queried once per
+        // device)
+        static std::atomic<uint32_t> waves[kMaxDevices];
+        int dev = 0;
+        cudaGetDevice(&dev);
+        uint32_t wave = (unsigned)dev < (unsigned)kMaxDevices ? waves[dev].load() : 0u;
         if (!wave) {
-            int dev = 0, sms = 0, per_sm = 0;
-            cudaGetDevice(&dev);
+            int sms = 0, per_sm = 0;
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, agent_stage1_kernel,
                                                           kAgentBlock, 0);
             wave = (uint32_t)(sms > 0 ? sms : 1) * (uint32_t)(per_sm > 0 ? per_sm : 1);
+            if ((unsigned)dev < (unsigned)kMaxDevices) waves[dev].store(wave);
         }
         const uint32_t front = agent_blocks < wave ? agent_blocks : wave;
         cudaError_t e = launch_pdl(agent_stage1_kernel, cell_blocks + agent_blocks,
