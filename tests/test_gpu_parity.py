@@ -142,6 +142,26 @@ def test_aco_2048_full_run():
     assert sim.device_status() == 0
 
 
+def test_more_agent_blocks_than_one_wave():
+    """400,000 agents (1,563 agent blocks): more proposal blocks than one
+    resident wave of the first agent kernel holds, so the ones beyond the
+    first wave are interleaved with the stream blocks; checked every step
+    against the oracle, and over a graph replay of 16 steps."""
+    sc = WL.Scenario(1024, 1024, WL.ACO, 200_000, 256, 31, 40, rho=0.05, deposit_mode=1,
+                     name="aco_1024x1024_400k_agents")
+    sim, orc = make_pair(sc)
+    for t in range(1, 5):
+        sim.step(1)
+        orc.step(1)
+        assert_same(sim, orc, f"{sc.name} step {t}")
+    sim.step(16)
+    orc.step(16)
+    assert_same(sim, orc, f"{sc.name} step 20")
+    assert sim.stats() == orc.stats()
+    assert sim.device_status() == 0
+    sim.close()
+
+
 EDGE = [
     WL.Scenario(32, 16, WL.ACO, 0, 4, 1, 160, rho=0.5, name="empty_grid_decay_to_subnormal"),
     WL.Scenario(64, 32, WL.ACO, 8 * 32, 8, 2, 60, rho=0.05, name="full_bands"),
