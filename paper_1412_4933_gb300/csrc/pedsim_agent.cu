@@ -6,14 +6,15 @@
 //     proposal blocks     one thread per agent: forward first, else the full
 //                         rule (Eq. 1 LEM rank draw, Eq. 2 ACO roulette) from
 //                         the occupancy and pheromone at t; the direction code
-//                         goes to the agent's cell of the proposal plane
+//                         goes to the agent's entry of `acode`, and its claim
+//                         bit (its scan offset seen from the target) is OR-ed
+//                         into the target's byte of the step's claim plane
 //     stream blocks       every cell: both pheromone planes evaporated into
 //                         the planes of t+1 (Eq. 3); a pure 16-byte-vector
 //                         stream, the HBM-bound part of the step (ACO only)
-//   agent_resolve_kernel  one thread per agent with a proposal: the claimants
-//                         of its target cell are read back from the proposal
-//                         plane (codes are valid exactly at cells occupied at
-//                         t), the winner is drawn as in Sec. IV.d, and the
+//   agent_resolve_kernel  one thread per agent with a proposal: the claim
+//                         mask of its target cell (all its claimants' bits),
+//                         the winner drawn from it as in Sec. IV.d, and the
 //                         winning agent moves: occupancy, id, position, tour
 //                         and arrival, and its deposit (Eq. 4/5) on top of the
 //                         evaporated value
