@@ -32,7 +32,7 @@ Also reported on the same line:
                 simulation's own L2-resident regime
   inputs_larger_than_l2
                 four independent copies of the headline scenario advanced
-                together (inputs 4 x ~95 MB > L2), graph replays timed with
+                together (inputs 4 x 101 MiB > L2), graph replays timed with
                 one event pair: the cold-L2 step without per-step events
   batched       256 uneven scenarios x 500 steps in the persistent batched
                 launch, vs one launch per scenario per step
@@ -63,7 +63,7 @@ sys.path.insert(0, ROOT)
 from paper_1412_4933_gb300 import workloads as WL  # noqa: E402
 
 L2_FLUSH_BYTES = 512 << 20
-ROTATING_INSTANCES = 4  # headline: 4 x ~95 MB of state, well above the 129 MB L2
+ROTATING_INSTANCES = 4  # headline: 4 x 101 MiB of state at 2048^2, well above the L2
 NOMINAL_HBM_GBPS = 7900.0  # GB300 HBM3e nominal, for context beside the measured peak
 ALGO_BYTES_PER_CELL = {WL.LEM: 2, WL.ACO: 18}
 KERNEL_SOURCES = ["paper_1412_4933_gb300/csrc/pedsim_agent.cu",
@@ -281,6 +281,20 @@ def rotating_instances(P, torch, sc, stream, variant, warmup: int, count: int):
 
 
 ROUNDS_PER_GRAPH = 4  # rounds of one step per instance in one graph replay
+L2_BYTES = 129 << 20  # GB300 L2
+
+
+def rotating_l2_note(P, sc) -> str:
+    """How the headline keeps its inputs out of L2, with the instances'
+    actual device state (the library's own size query)."""
+    each = P.device_bytes(sc.W, sc.H, P.params_of(sc))
+    total = ROTATING_INSTANCES * each
+    where = ("inputs larger than L2: every step reads its state from HBM" if total > L2_BYTES
+             else "inputs fit in L2 together (this workload is launch-bound, not HBM-bound)")
+    return (f"{where}; {ROTATING_INSTANCES} resident instances of the workload (seeds "
+            f"{sc.seed}..{sc.seed + ROTATING_INSTANCES - 1}, {each / 2**20:.0f} MiB of device "
+            f"state each, {total / 2**20:.0f} MiB in all against the {L2_BYTES >> 20} MiB L2) "
+            f"stepped in turn, one step each; one event pair around all steps")
 
 
 def capture_rounds(sims, torch, stream, rounds: int):
@@ -380,7 +394,7 @@ def e2e_run(P, torch, sc, stream, reps: int):
 
 def large_inputs_leg(P, torch, sc, stream, instances=4, steps=96):
     """The headline scenario with inputs larger than L2 instead of a flush:
-    `instances` independent copies (seeds sc.seed + k; 4 x ~95 MB > 129 MB
+    `instances` independent copies (seeds sc.seed + k; 4 x 101 MiB > 129 MB
     L2) advanced together as a batch, so every step streams its planes from
     HBM; graph replays timed with one event pair (no per-step events)."""
     scs = [sc.with_(seed=sc.seed + k, name=f"{sc.name}#{k}") for k in range(instances)]
@@ -611,10 +625,7 @@ def run_gpu(args, sc):
             "config": {"workload": sc.name, "W": sc.W, "H": sc.H, "agents": sc.agents,
                        "model": "ACO" if sc.model else "LEM", "rho": sc.rho, "seed": sc.seed,
                        "band_cols": sc.band_cols,
-                       "l2": f"inputs larger than L2: {ROTATING_INSTANCES} resident instances of "
-                             f"the workload (seeds {sc.seed}..{sc.seed + ROTATING_INSTANCES - 1}, "
-                             f"~95 MB of state each) stepped in turn, one step each, so every "
-                             f"step reads its state from HBM; one event pair around all steps",
+                       "l2": rotating_l2_note(P, sc),
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks, "gpu_launches": launches * args.steps,
