@@ -35,6 +35,7 @@
 #include "pedsim_rules.cuh"
 #include "pedsim_ptx.cuh"
 
+
 namespace pedsim {
 
 constexpr int kMaxDevices = 64;  // devices whose occupancy is cached
@@ -147,6 +148,8 @@ agent_stage1_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__re
     // the resolution kernel be scheduled (it waits for this one).
     pdl_wait();
     pdl_trigger();
+    // (cell_blocks here counts the blocks this kernel streams: the first
+    // ones; the resolution kernel evaporates the rest)
     // CTAs 0 .. front-1 are the first proposal blocks (at most one resident
     // wave): proposal CTAs (latency chains, longer in congestion) start at
     // once and end before the stream's tail, which measured faster than an
@@ -189,6 +192,65 @@ agent_stage1_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__re
     }
 }
 
+// Evaporation of cell block b in the resolution kernel, where the claims of
+// the step are final: the loads of the planes of t (which the first kernel
+// does not write) are issued before the wait for the first kernel, the
+// claim bytes after it, and claimed cells are left to their winners.
+__device__ __forceinline__ void stream_block_claimed(const ScenarioDesc *__restrict__ descs,
+                                                     const uint32_t *__restrict__ cell_prefix,
+                                                     int n_scen, uint32_t b)
+{
+    const int s = block_scenario(cell_prefix, n_scen, b);
+    const ScenarioDesc &d = descs[s];
+    const uint64_t t = d.step;
+    const bool active = t < d.end_step;
+    const size_t cells = (size_t)d.W * (size_t)d.H;
+    const size_t c0 = (size_t)(b - __ldg(cell_prefix + s)) * kCellBlock;
+    const int p = (int)(t & 1);
+    float4 va[kStreamVec], vb[kStreamVec];
+#pragma unroll
+    for (int k = 0; k < kStreamVec; ++k) {
+        const size_t c = c0 + 4 * ((size_t)k * kAgentBlock + threadIdx.x);
+        if (active && c < cells) {
+            va[k] = __ldcg(reinterpret_cast<const float4 *>(d.tau[0][p] + c));
+            vb[k] = __ldcg(reinterpret_cast<const float4 *>(d.tau[1][p] + c));
+        }
+    }
+    pdl_wait();  // the claims of the step are in
+    pdl_trigger();
+    if (!active) return;
+    uint32_t cw[kStreamVec];
+#pragma unroll
+    for (int k = 0; k < kStreamVec; ++k) {
+        const size_t c = c0 + 4 * ((size_t)k * kAgentBlock + threadIdx.x);
+        cw[k] = c < cells ? __ldcg(reinterpret_cast<const unsigned int *>(d.claim[p] + c)) : 0u;
+    }
+    const float q = d.q;
+    float *const na = d.tau[0][p ^ 1], *const nb = d.tau[1][p ^ 1];
+#pragma unroll
+    for (int k = 0; k < kStreamVec; ++k) {
+        const size_t c = c0 + 4 * ((size_t)k * kAgentBlock + threadIdx.x);
+        if (c >= cells) continue;
+        const float a_[4] = {va[k].x, va[k].y, va[k].z, va[k].w};
+        const float b_[4] = {vb[k].x, vb[k].y, vb[k].z, vb[k].w};
+        if (cw[k] == 0u) {
+            *reinterpret_cast<float4 *>(na + c) =
+                make_float4(__fmul_rn(a_[0], q), __fmul_rn(a_[1], q), __fmul_rn(a_[2], q),
+                            __fmul_rn(a_[3], q));
+            *reinterpret_cast<float4 *>(nb + c) =
+                make_float4(__fmul_rn(b_[0], q), __fmul_rn(b_[1], q), __fmul_rn(b_[2], q),
+                            __fmul_rn(b_[3], q));
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if ((cw[k] >> (8 * j)) & 0xffu) continue;  // the winner stores this cell
+                na[c + j] = __fmul_rn(a_[j], q);
+                nb[c + j] = __fmul_rn(b_[j], q);
+            }
+        }
+    }
+}
+
 // Resolution work of one agent: its own entries (first round of loads) and
 // its target's neighbourhood (second round).  Nothing read here is written
 // by the resolution kernel before it is read (position and per-agent entries
@@ -201,7 +263,9 @@ struct Resolve {
     uint32_t arrived;
     int64_t target;
     uint32_t mask;
-    float tau_t;
+    float tau_t;  // own group's pheromone at the target, at t
+    float tau_o;  // the other group's (targets in cell blocks evaporated late)
+    bool late;    // the target's cell block is evaporated in the resolution kernel
 };
 
 __device__ __forceinline__ void resolve_load_own(const ScenarioDesc &d, uint32_t a, Resolve &r)
@@ -218,12 +282,17 @@ __device__ __forceinline__ void resolve_load_own(const ScenarioDesc &d, uint32_t
 // Claim mask of the target (bit j: its claimant at scan offset j; every
 // claimant's proposal pass has OR-ed its bit in) and the target's own-group
 // pheromone at t.
-__device__ __forceinline__ void resolve_load_target(const ScenarioDesc &d, uint64_t t, Resolve &r)
+// late_from: the scenario's first cell block evaporated in the resolution
+// kernel (its cell blocks from there on skip claimed cells).
+__device__ __forceinline__ void resolve_load_target(const ScenarioDesc &d, uint64_t t, Resolve &r,
+                                                    uint32_t late_from)
 {
     const int W = d.W;
     const int p = (int)(t & 1);
     r.target = (int64_t)r.cell + (int64_t)kCodeDY[r.code] * W + kCodeDX[r.code];
+    r.late = (uint64_t)r.target / kCellBlock >= late_from;
     r.tau_t = d.model == 1 ? __ldg(d.tau[r.g == 2 ? 1 : 0][p] + r.target) : 0.0f;
+    r.tau_o = d.model == 1 && r.late ? __ldg(d.tau[r.g == 2 ? 0 : 1][p] + r.target) : 0.0f;
     r.mask = __ldg(d.claim[p] + r.target);
 }
 
@@ -257,8 +326,13 @@ __device__ __forceinline__ void resolve_apply(const ScenarioDesc &d, uint64_t t,
         d.arrival[r.id] = (uint32_t)(t + 1);
         if (g == 1) ++cnt.crossed_a; else ++cnt.crossed_b;
     }
-    // the evaporated value (what the stream blocks wrote) plus the deposit
-    if (d.model == 1) d.tau[g == 2 ? 1 : 0][p ^ 1][r.target] = __fadd_rn(__fmul_rn(r.tau_t, d.q), dep);
+    // the own group's evaporated value plus the deposit; in a cell block
+    // evaporated in the resolution kernel (which skips claimed cells) also
+    // the other group's evaporated value
+    if (d.model == 1) {
+        d.tau[g == 2 ? 1 : 0][p ^ 1][r.target] = __fadd_rn(__fmul_rn(r.tau_t, d.q), dep);
+        if (r.late) d.tau[g == 2 ? 0 : 1][p ^ 1][r.target] = __fmul_rn(r.tau_o, d.q);
+    }
     ++cnt.moved;
     if (k >= 2) ++cnt.conflicts;
 }
@@ -266,17 +340,44 @@ __device__ __forceinline__ void resolve_apply(const ScenarioDesc &d, uint64_t t,
 // Each CTA resolves kResolveBlocks consecutive agent blocks, one agent of
 // each per thread, with the loads of all of them in flight together (1: 2
 // and 4 were measured slower at 2048^2 and 8192^2).
-constexpr int kResolveBlocks = 1;
+constexpr int kResolveBlocks = 1;  // the resolution kernel's CTA indices assume 1
 
 __global__ void __launch_bounds__(kAgentBlock)
 agent_resolve_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__restrict__ agent_prefix,
-                     int n_scen, uint32_t agent_blocks, ActivityCtl *__restrict__ ctl)
+                     const uint32_t *__restrict__ cell_prefix, int n_scen, uint32_t agent_blocks,
+                     uint32_t first_late, uint32_t late_blocks, ActivityCtl *__restrict__ ctl)
 {
+    if (blockIdx.x >= agent_blocks) {
+        // CTAs past the agent blocks evaporate cell blocks first_late .. ;
+        // every CTA takes a ticket once its threads hold the step index
+        const uint32_t b = first_late + (blockIdx.x - agent_blocks);
+        if (b < first_late + late_blocks) stream_block_claimed(descs, cell_prefix, n_scen, b);
+        else {
+            pdl_wait();
+            pdl_trigger();
+        }
+        __syncthreads();
+        unsigned int ticket = 0;
+        if (threadIdx.x == 0) ticket = atomicAdd(&ctl->ticket, 1u);
+        if (threadIdx.x < 32) {
+            const bool last = __shfl_sync(0xffffffffu, ticket == gridDim.x - 1, 0);
+            if (last) {
+                ScenarioDesc *md = const_cast<ScenarioDesc *>(descs);
+                for (int i = threadIdx.x; i < n_scen; i += 32) {
+                    const unsigned long long v = md[i].step;
+                    if (v < md[i].end_step) md[i].step = v + 1;
+                }
+                if (threadIdx.x == 0) ctl->ticket = 0u;
+            }
+        }
+        return;
+    }
     pdl_wait();  // first kernel (proposals and stream) complete
     pdl_trigger();
     const ScenarioDesc *dq[kResolveBlocks];
     uint32_t lb[kResolveBlocks];
     uint64_t tq[kResolveBlocks];
+    uint32_t late_from[kResolveBlocks];
     bool live[kResolveBlocks];
     Resolve r[kResolveBlocks];
 #pragma unroll
@@ -286,11 +387,14 @@ agent_resolve_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__r
         dq[q] = descs;
         lb[q] = 0;
         tq[q] = 0;
+        late_from[q] = 0;
         if (b >= agent_blocks) continue;
         const int s = block_scenario(agent_prefix, n_scen, b);
         dq[q] = descs + s;
         lb[q] = b - __ldg(agent_prefix + s);
         tq[q] = dq[q]->step;
+        const uint32_t cp = __ldg(cell_prefix + s);
+        late_from[q] = first_late > cp ? first_late - cp : 0u;
         const uint32_t a = lb[q] * kAgentBlock + threadIdx.x;
         live[q] = tq[q] < dq[q]->end_step && a < 2u * dq[q]->n_per_side;
         if (live[q]) resolve_load_own(*dq[q], a, r[q]);
@@ -305,7 +409,7 @@ agent_resolve_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__r
     if (threadIdx.x == 0) ticket = atomicAdd(&ctl->ticket, 1u);
 #pragma unroll
     for (int q = 0; q < kResolveBlocks; ++q)
-        if (live[q]) resolve_load_target(*dq[q], tq[q], r[q]);
+        if (live[q]) resolve_load_target(*dq[q], tq[q], r[q], late_from[q]);
 #pragma unroll
     for (int q = 0; q < kResolveBlocks; ++q) {
         Counts cnt;
@@ -343,42 +447,86 @@ __global__ void build_pos_kernel(const ScenarioDesc *__restrict__ dp, int plane)
         d.acode[a] = 0;
 }
 
+// Resident CTAs of one wave of a kernel on the current device (occupancy
+// queried once per device and kernel; the queries also run when a scenario
+// is placed or loaded, so that no first query falls inside a caller's
+// stream capture).
+template <class Kernel>
+static uint32_t resident_wave(Kernel kernel, std::atomic<uint32_t> (&cache)[kMaxDevices])
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    uint32_t wave = (unsigned)dev < (unsigned)kMaxDevices ? cache[dev].load() : 0u;
+    if (!wave) {
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kAgentBlock, 0);
+        wave = (uint32_t)(sms > 0 ? sms : 1) * (uint32_t)(per_sm > 0 ? per_sm : 1);
+        if ((unsigned)dev < (unsigned)kMaxDevices) cache[dev].store(wave);
+    }
+    return wave;
+}
+
+static uint32_t stage1_wave()
+{
+    static std::atomic<uint32_t> cache[kMaxDevices];
+    return resident_wave(agent_stage1_kernel, cache);
+}
+
+static uint32_t resolve_wave()
+{
+    static std::atomic<uint32_t> cache[kMaxDevices];
+    return resident_wave(agent_resolve_kernel, cache);
+}
+
+// Cell blocks of a step evaporated in the resolution kernel: the free part
+// of one resident wave of that kernel, at most all but one cell block (the
+// first kernel must run whenever there are cell blocks: the resolution
+// kernel's loads before its wait rely on the first kernel having waited for
+// the previous step).
+static uint32_t resolve_late_blocks(uint32_t cell_blocks, uint32_t agent_blocks)
+{
+    const uint32_t wave = resolve_wave();
+    if (cell_blocks == 0 || agent_blocks >= wave) return 0;
+    const uint32_t free = wave - agent_blocks;
+    return free < cell_blocks - 1 ? free : cell_blocks - 1;
+}
+
 cudaError_t launch_agent_step(const ScenarioDesc *d_descs, const uint32_t *d_cell_prefix,
                               const uint32_t *d_agent_prefix, int n, uint32_t cell_blocks,
                               uint32_t agent_blocks, ActivityCtl *ctl, cudaStream_t stream)
 {
     if (n <= 0) return cudaSuccess;
+    // Cell blocks evaporated in the resolution kernel (the claims are final
+    // there, so they skip claimed cells): as many as fill that kernel up to
+    // one resident wave beside its agent CTAs, which alone leave most of the
+    // GPU idle at a few hundred CTAs, and never all of them (the first
+    // kernel keeps at least one, see resolve_late_blocks).
+    const uint32_t late = resolve_late_blocks(cell_blocks, agent_blocks);
     if (cell_blocks + agent_blocks) {
-        // one resident wave of the first kernel (occupancy queried once per
-        // device)
-        static std::atomic<uint32_t> waves[kMaxDevices];
-        int dev = 0;
-        cudaGetDevice(&dev);
-        uint32_t wave = (unsigned)dev < (unsigned)kMaxDevices ? waves[dev].load() : 0u;
-        if (!wave) {
-            int sms = 0, per_sm = 0;
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, agent_stage1_kernel,
-                                                          kAgentBlock, 0);
-            wave = (uint32_t)(sms > 0 ? sms : 1) * (uint32_t)(per_sm > 0 ? per_sm : 1);
-            if ((unsigned)dev < (unsigned)kMaxDevices) waves[dev].store(wave);
-        }
+        const uint32_t wave = stage1_wave();
         const uint32_t front = agent_blocks < wave ? agent_blocks : wave;
-        cudaError_t e = launch_pdl(agent_stage1_kernel, cell_blocks + agent_blocks,
-                                   (unsigned)kAgentBlock, stream, d_descs, d_cell_prefix,
-                                   d_agent_prefix, n, cell_blocks, agent_blocks, front);
-
-        if (e != cudaSuccess) return e;
+        const uint32_t c1 = cell_blocks - late;
+        if (c1 + agent_blocks) {
+            cudaError_t e = launch_pdl(agent_stage1_kernel, c1 + agent_blocks,
+                                       (unsigned)kAgentBlock, stream, d_descs, d_cell_prefix,
+                                       d_agent_prefix, n, c1, agent_blocks, front);
+            if (e != cudaSuccess) return e;
+        }
     }
-    // the resolution kernel also advances the step index: with no agent it
-    // is one CTA that does only that
-    const uint32_t g = agent_blocks ? (agent_blocks + kResolveBlocks - 1) / kResolveBlocks : 1u;
+    // the resolution kernel also evaporates the last `late` cell blocks and
+    // advances the step index: with no agent and no such block it is one CTA
+    // that does only that
+    const uint32_t g = agent_blocks + late > 0 ? agent_blocks + late : 1u;
     return launch_pdl(agent_resolve_kernel, g, (unsigned)kAgentBlock, stream, d_descs,
-                      d_agent_prefix, n, agent_blocks, ctl);
+                      d_agent_prefix, d_cell_prefix, n, agent_blocks, cell_blocks - late, late,
+                      ctl);
 }
 
 cudaError_t launch_build_pos(const ScenarioDesc *d_desc, int cells, int plane, cudaStream_t stream)
 {
+    (void)stage1_wave();  // the step's occupancy queries, outside any capture
+    (void)resolve_wave();
     int blocks = (cells + 255) / 256;
     if (blocks > 1024) blocks = 1024;
     if (blocks < 1) blocks = 1;
