@@ -178,10 +178,13 @@ int sim_load(sim_t *s, const void *buf, size_t len);
  *                         rule, the others only evaporate
  * PEDSIM_VARIANT_AGENT    (default) two kernels per step: one thread per agent
  *                         computes its proposal while the other CTAs of the
- *                         same kernel stream every cell's pheromone
- *                         evaporation; then one thread per agent resolves its
- *                         target cell, applies the winner's move and deposit
- *                         and the last CTA advances the step index
+ *                         same kernel stream the pheromone evaporation of
+ *                         most cells; then one thread per agent resolves its
+ *                         target cell and applies the winner's move and
+ *                         deposit, while further CTAs evaporate the remaining
+ *                         cells (skipping the claimed ones, which their
+ *                         winners write), and the last CTA advances the step
+ *                         index
  * Selecting a variant resets the tile shape to its default (tiled: 128 x 16;
  * fused: 64 x 16; the agent variant has none).                                */
 #define PEDSIM_VARIANT_TILED    0
