@@ -17,7 +17,10 @@
 //                         the winner drawn from it as in Sec. IV.d, and the
 //                         winning agent moves: occupancy, id, position, tour
 //                         and arrival, and its deposit (Eq. 4/5) on top of the
-//                         evaporated value
+//                         evaporated value; beside the agent CTAs, stream CTAs
+//                         evaporate the step's last cell blocks (as many as
+//                         fill one resident wave), skipping the claimed cells,
+//                         whose winners write both planes
 //
 // Occupancy lives in one plane, occ[0], updated in place: the proposals read
 // it (state at t) in the first kernel, the moves are applied to it only in
