@@ -254,11 +254,12 @@ __device__ __forceinline__ void stream_block_claimed(const ScenarioDesc *__restr
     }
 }
 
-// Resolution work of one agent: its own entries (first round of loads) and
-// its target's neighbourhood (second round).  Nothing read here is written
+// Resolution work of one agent: its own entries (position, tour and arrival
+// before the wait for the first kernel, its code after it) and its target's
+// claim mask and pheromone (a second round).  Nothing read here is written
 // by the resolution kernel before it is read (position and per-agent entries
-// only by their own thread, after reading), so the loads take the read-only
-// cached path and the rounds of several agents overlap.
+// only by their own thread, after reading), and the rounds of several agents
+// overlap.
 struct Resolve {
     uint32_t id, cell;
     int code, g;
@@ -271,15 +272,23 @@ struct Resolve {
     bool late;    // the target's cell block is evaporated in the resolution kernel
 };
 
+// The agent's entries the first kernel does not write (written by the
+// previous step's resolution, complete before the first kernel began):
+// loaded before the wait for the first kernel.
 __device__ __forceinline__ void resolve_load_own(const ScenarioDesc &d, uint32_t a, Resolve &r)
 {
     r.id = a + 1u;
-    r.cell = __ldg(d.pos + r.id);
-    const int ac = __ldg(d.acode + r.id);
+    r.cell = __ldcg(d.pos + r.id);
+    r.tour0 = (d.model == 1 && d.deposit_mode == 1) ? __ldcg(d.tour + r.id) : 0.0f;
+    r.arrived = __ldcg(d.arrival + r.id);
+}
+
+// This step's proposal code and the agent's group (first kernel's output).
+__device__ __forceinline__ void resolve_load_code(const ScenarioDesc &d, Resolve &r)
+{
+    const int ac = __ldcg(d.acode + r.id);
     r.code = ac & 15;
     r.g = ac >> 4;
-    r.tour0 = (d.model == 1 && d.deposit_mode == 1) ? __ldg(d.tour + r.id) : 0.0f;
-    r.arrived = __ldg(d.arrival + r.id);
 }
 
 // Claim mask of the target (bit j: its claimant at scan offset j; every
@@ -375,8 +384,6 @@ agent_resolve_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__r
         }
         return;
     }
-    pdl_wait();  // first kernel (proposals and stream) complete
-    pdl_trigger();
     const ScenarioDesc *dq[kResolveBlocks];
     uint32_t lb[kResolveBlocks];
     uint64_t tq[kResolveBlocks];
@@ -401,6 +408,12 @@ agent_resolve_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__r
         const uint32_t a = lb[q] * kAgentBlock + threadIdx.x;
         live[q] = tq[q] < dq[q]->end_step && a < 2u * dq[q]->n_per_side;
         if (live[q]) resolve_load_own(*dq[q], a, r[q]);
+    }
+    pdl_wait();  // first kernel (proposals and stream) complete
+    pdl_trigger();
+#pragma unroll
+    for (int q = 0; q < kResolveBlocks; ++q) {
+        if (live[q]) resolve_load_code(*dq[q], r[q]);
         if (live[q] && r[q].code == 0) live[q] = false;
     }
     // Every thread of the CTA has read its step index: the CTA takes its
