@@ -6,10 +6,12 @@ one "step" = one synchronous automaton step (proposal, gather resolution,
 move, evaporation + deposit, counters) over the whole grid, inputs resident
 in HBM.  One scenario's working set (~92 MB) would stay in the 129 MB L2,
 so the timed steps take inputs larger than L2: four resident instances of
-the workload (seeds 3..6) are stepped in turn, one single-scenario step
-each (CUDA graphs of four rounds, replayed), so every step reads its state
-from HBM and the write-backs of earlier steps land inside the timed region;
-one event pair around all K steps.
+the workload (seeds 3..6, each after --warmup untimed steps) are stepped in
+turn, one single-scenario step each, so every step reads its state from HBM
+and the write-backs of earlier steps land inside the timed region.  The K
+timed steps are one CUDA graph of exactly K steps; after one untimed replay
+it is replayed --repeats times, each replay timed with one event pair
+between barriers, and the headline is the median region.
 
 Also reported on the same line:
   flushed_per_step
@@ -280,8 +282,8 @@ def rotating_instances(P, torch, sc, stream, variant, warmup: int, count: int):
     return sims
 
 
-ROUNDS_PER_GRAPH = 4  # rounds of one step per instance in one graph replay
 L2_BYTES = 129 << 20  # GB300 L2
+HEADLINE_REPEATS = 5  # timed regions of exactly K steps each; the headline is their median
 
 
 def rotating_l2_note(P, sc) -> str:
@@ -294,45 +296,44 @@ def rotating_l2_note(P, sc) -> str:
     return (f"{where}; {ROTATING_INSTANCES} resident instances of the workload (seeds "
             f"{sc.seed}..{sc.seed + ROTATING_INSTANCES - 1}, {each / 2**20:.0f} MiB of device "
             f"state each, {total / 2**20:.0f} MiB in all against the {L2_BYTES >> 20} MiB L2) "
-            f"stepped in turn, one step each; one event pair around all steps")
+            f"stepped in turn, one step each, from one CUDA graph of exactly the timed steps; "
+            f"one event pair around each replay")
 
 
-def capture_rounds(sims, torch, stream, rounds: int):
-    """`rounds` rounds of one step of every instance in turn, captured as one
-    CUDA graph (the library's launches go into the capturing stream; kernels
-    of consecutive steps overlap by programmatic dependent launch only
-    inside a graph) and replayed once."""
+def capture_steps(sims, torch, stream, steps: int):
+    """One CUDA graph of exactly `steps` single-scenario steps, step i
+    advancing instance i % len(sims) (the library's launches go into the
+    capturing stream; consecutive kernels overlap by programmatic dependent
+    launch inside the graph)."""
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=stream):
-        for _ in range(rounds):
-            for s in sims:
-                s.step(1)
-    with torch.cuda.stream(stream):
-        g.replay()
+        for i in range(steps):
+            sims[i % len(sims)].step(1)
     torch.cuda.synchronize()
     return g
 
 
-def time_steps_rotating(sims, graphs, torch, stream, steps: int) -> float:
-    """Seconds for `steps` single-scenario steps, step i advancing instance
-    i % len(sims) (replays of the ROUNDS_PER_GRAPH-round graph, then of the
-    one-round graph, then single steps), with one event pair around all of
-    them."""
-    big, one = graphs
-    rounds, rem = divmod(steps, len(sims))
-    n_big, n_one = divmod(rounds, ROUNDS_PER_GRAPH)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+def time_graph_repeats(graph, torch, stream, repeats: int, dist=None, device=None):
+    """Replays `graph` once untimed (graph upload, more warm-up), then
+    `repeats` times, each replay bracketed by a barrier, a device
+    synchronisation and one CUDA-event pair on the launching stream.
+    Returns the max-over-ranks seconds of each timed replay."""
     with torch.cuda.stream(stream):
-        for _ in range(n_big):
-            big.replay()
-        for _ in range(n_one):
-            one.replay()
-        for s in sims[:rem]:
-            s.step(1)
-    e1.record(stream)
+        graph.replay()
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1) * 1e-3
+    out = []
+    for _ in range(repeats):
+        barrier(dist, device)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(dist, device)
+        out.append(max_over_ranks(e0.elapsed_time(e1) * 1e-3, dist, device))
+    return out
 
 
 def time_steps_flushed(sim, torch, stream, steps: int, flush):
@@ -386,9 +387,13 @@ def e2e_run(P, torch, sc, stream, reps: int):
     sim.close()
     best = statistics.median(times)
     return {"value": sc.cells * sc.steps / best, "unit": "cell-updates/s",
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "step": f"one {sc.steps}-step run of {sc.name}: H2D of the initial state from pinned "
-                    f"memory, {sc.steps} automaton steps, D2H of the final grid + counters",
+            "h2d_bytes_per_step": h2d / sc.steps, "d2h_bytes_per_step": d2h / sc.steps,
+            "h2d_bytes_per_run": h2d, "d2h_bytes_per_run": d2h,
+            "run": f"one {sc.steps}-step run of {sc.name} through the C ABI: H2D of the initial "
+                   f"state from pinned memory, {sc.steps} automaton steps, D2H of the final grid "
+                   f"+ counters; per-step bytes are the run's bytes / {sc.steps}",
+            "l2": "a single instance: its state stays in the L2 across the run's steps (the "
+                  "simulation's own regime), unlike the headline's four instances in turn",
             "seconds_per_run": best, "final_moved": st["moved"]}
 
 
@@ -529,18 +534,16 @@ def run_gpu(args, sc):
     # workload, stepped in turn, so that every step reads its state from HBM
     sims = rotating_instances(P, torch, sc, stream, variant, args.warmup, ROTATING_INSTANCES)
     sim = sims[0]
-    graphs = (capture_rounds(sims, torch, stream, ROUNDS_PER_GRAPH),
-              capture_rounds(sims, torch, stream, 1))
+    graph = capture_steps(sims, torch, stream, args.steps)
     barrier(dist, device)
 
     with ClockSampler(local) as clk:
-        elapsed = time_steps_rotating(sims, graphs, torch, stream, args.steps)
-    barrier(dist, device)
-    elapsed_max = max_over_ranks(elapsed, dist, device)
+        region_s = time_graph_repeats(graph, torch, stream, args.repeats, dist, device)
+    elapsed_max = statistics.median(region_s)
     clocks = clk.summary()
     status = max(abs(x.device_status()) for x in sims)
     launches = sim.launches_per_step()
-    del graphs
+    del graph
     for x in sims[1:]:
         x.close()
     # the same single-scenario step with the L2 flushed before each step and
@@ -558,7 +561,7 @@ def run_gpu(args, sc):
     # bound of the streaming part's rate
     algo_bytes = ALGO_BYTES_PER_CELL[sc.model] * sc.cells
     peak, peak_kind = measured_peak()
-    step_s = elapsed / args.steps
+    step_s = elapsed_max / args.steps
     achieved = algo_bytes / step_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac_of_nominal": achieved / NOMINAL_HBM_GBPS, "nominal_peak": NOMINAL_HBM_GBPS,
@@ -628,6 +631,14 @@ def run_gpu(args, sc):
                        "l2": rotating_l2_note(P, sc),
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "timed_regions": {
+                "repeats": len(region_s), "steps_each": args.steps,
+                "us_per_step": [r * 1e6 / args.steps for r in region_s],
+                "median_us_per_step": elapsed_max * 1e6 / args.steps,
+                "spread_us_per_step": (max(region_s) - min(region_s)) * 1e6 / args.steps,
+                "note": "each region is one replay of one CUDA graph of exactly `steps` steps "
+                        "(instances in turn), after one untimed replay; value and ms_per_step "
+                        "are the median region"},
             "clocks": clocks, "gpu_launches": launches * args.steps,
             "device_status": status,
         }
@@ -643,6 +654,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--repeats", type=int, default=HEADLINE_REPEATS,
+                    help="timed regions of exactly --steps steps; the headline is their median")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WL.ACO_2048.name, choices=sorted(WL.SINGLE))
     ap.add_argument("--variant", default="agent", choices=sorted(VARIANTS),
@@ -657,6 +670,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.repeats < 1 or args.steps < 1:
+        ap.error("--repeats and --steps must be >= 1")
     sc = WL.SINGLE[args.workload]
     if args.impl == "reference":
         return run_reference(args, sc)

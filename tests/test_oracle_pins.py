@@ -445,3 +445,156 @@ def test_parameter_validation():
            (64, 64, O.make_params(model=0, n_per_side=10, band_cols=0))]
     for W, H, prm in bad:
         assert L.orc_check_params(W, H, O.C.byref(prm)) != 0, (W, H)
+
+
+# --------------------------------------------------------------------------
+# Eq. 5 tour length with diagonal moves: L_k grows by 1 per orthogonal move
+# and by fl(sqrt 2) per diagonal one, before the deposit 1/L_k (Sec. IV.d)
+# --------------------------------------------------------------------------
+def _f32_sqrt2_from_decimal():
+    getcontext().prec = 60
+    return _nearest_f32(Decimal(2).sqrt())
+
+
+def test_diagonal_step_tour_is_rounded_sqrt2():
+    # An A agent one column before its goal edge, its forward cell held by a
+    # parked A agent: forward is blocked for good, so it moves sideways or
+    # diagonally (a forward diagonal parks it).  Over seeds where that first
+    # move is diagonal, the tour must be fl(sqrt 2) and the deposit fl(1/L)
+    # on top of the evaporated value.
+    W, H, y = 32, 16, 8
+    rho, tau0 = 0.05, 0.75
+    sqrt2 = _f32_sqrt2_from_decimal()
+    f32 = np.float32
+    q = f32(1.0) - f32(rho)
+    diag_seen = orth_seen = 0
+    for seed in range(60):
+        occ = np.zeros((H, W), np.uint8); ids = np.zeros((H, W), np.uint32)
+        occ[y, W - 2] = 1; ids[y, W - 2] = 1    # the walker
+        occ[y, W - 1] = 1; ids[y, W - 1] = 2    # parked on the goal column
+        p = O.make_params(model=1, n_per_side=1, band_cols=4, rho=rho, tau0=tau0,
+                          deposit_mode=1)
+        o = O.Oracle(W, H, p, seed, state={"occ": occ, "ids": ids})
+        o.step(1)
+        st = o.state()
+        (ny,), (nx,) = np.nonzero(st["ids"] == 1)
+        dx, dy = nx - (W - 2), ny - y
+        if dx == 0 and dy == 0:
+            continue
+        if dx != 0 and dy != 0:
+            diag_seen += 1
+            assert st["tour"][1] == sqrt2, seed
+            want = f32(f32(f32(tau0) * q) + f32(f32(1.0) / sqrt2))
+        else:
+            orth_seen += 1
+            assert st["tour"][1] == f32(1.0), seed
+            want = f32(f32(f32(tau0) * q) + f32(1.0))
+        assert st["tauA"][ny, nx].view(np.uint32) == want.view(np.uint32), seed
+    # the forward diagonals are the most likely ranks of Eq. 2
+    assert diag_seen >= 20 and orth_seen >= 1, (diag_seen, orth_seen)
+
+
+def test_tour_and_deposit_follow_the_moves_of_a_dense_run():
+    # Dense ACO run with Eq. 5 deposits: from the ids plane of consecutive
+    # states, recompute every agent's tour (1 per orthogonal and fl(sqrt 2)
+    # per diagonal move, summed in move order) and both pheromone planes
+    # (evaporate every cell, then add fl(1/L) of each mover at its new cell).
+    W, H, n, rho = 48, 32, 300, 0.07
+    sqrt2 = _f32_sqrt2_from_decimal()
+    f32 = np.float32
+    q = f32(1.0) - f32(rho)
+    p = O.make_params(model=1, n_per_side=n, band_cols=16, rho=rho, tau0=1.0,
+                      deposit_mode=1)
+    o = O.Oracle(W, H, p, 31)
+    st = o.state()
+    N = 2 * n
+    pos = np.zeros((N + 1, 2), np.int64)
+    for yy, xx in zip(*np.nonzero(st["ids"])):
+        pos[st["ids"][yy, xx]] = (xx, yy)
+    tour = np.zeros(N + 1, np.float32)
+    tau = [st["tauA"].copy(), st["tauB"].copy()]
+    group = np.zeros(N + 1, np.int64)
+    group[st["ids"][st["occ"] != 0]] = st["occ"][st["occ"] != 0]
+    diag_moves = 0
+    for t in range(80):
+        o.step(1)
+        nxt = o.state()
+        tau = [(tp * q).astype(np.float32) for tp in tau]
+        for yy, xx in zip(*np.nonzero(nxt["ids"])):
+            a = nxt["ids"][yy, xx]
+            dx, dy = xx - pos[a][0], yy - pos[a][1]
+            if dx == 0 and dy == 0:
+                continue
+            assert max(abs(dx), abs(dy)) == 1, (t, a)
+            diag = dx != 0 and dy != 0
+            diag_moves += diag
+            tour[a] = f32(tour[a] + (sqrt2 if diag else f32(1.0)))
+            g = group[a] - 1
+            tau[g][yy, xx] = f32(tau[g][yy, xx] + f32(f32(1.0) / tour[a]))
+            pos[a] = (xx, yy)
+        assert np.array_equal(nxt["tour"].view(np.uint32), tour.view(np.uint32)), t
+        assert np.array_equal(nxt["tauA"].view(np.uint32), tau[0].view(np.uint32)), t
+        assert np.array_equal(nxt["tauB"].view(np.uint32), tau[1].view(np.uint32)), t
+    assert diag_moves > 200, diag_moves
+
+
+# --------------------------------------------------------------------------
+# Conflict counter (Sec. IV.d): the number of (cell, step) pairs with two or
+# more claimants -- cells, not losing agents
+# --------------------------------------------------------------------------
+def test_head_on_conflict_one_winner_each_side_half_the_time():
+    W, H, x, y = 32, 16, 10, 6
+    wins = 0
+    seeds = 400
+    for seed in range(seeds):
+        occ = np.zeros((H, W), np.uint8); ids = np.zeros((H, W), np.uint32)
+        occ[y, x] = 1; ids[y, x] = 1          # A heading +x
+        occ[y, x + 2] = 2; ids[y, x + 2] = 2  # B heading -x: both forward into x+1
+        p = O.make_params(model=0, n_per_side=1, band_cols=4)
+        o = O.Oracle(W, H, p, seed, state={"occ": occ, "ids": ids})
+        o.step(1)
+        s, st = o.stats(), o.state()
+        assert s["moved"] == 1 and s["conflicts"] == 1, (seed, s)
+        winner = int(st["ids"][y, x + 1])
+        assert winner in (1, 2)
+        loser_cell = (y, x + 2) if winner == 1 else (y, x)
+        assert st["ids"][loser_cell] == 3 - winner  # the loser stays
+        wins += winner == 1
+    # binomial(400, 1/2): 4.5 standard deviations either side
+    assert abs(wins - seeds / 2) < 4.5 * math.sqrt(seeds / 4), wins
+
+
+def test_conflict_counter_counts_cells_not_losers():
+    # Dense random states: every agent's decision at the step is taken from
+    # the oracle's own decision hook, then the claimants of every empty cell
+    # are counted here.  moved must be the number of claimed cells and
+    # conflicts the number of cells with >= 2 claimants; states with three
+    # or more claimants on one cell make the two readings differ.
+    W, H = 32, 32
+    rng = np.random.default_rng(8)
+    k3_cells = 0
+    for trial in range(40):
+        model = trial % 2
+        occ, _ = WL.random_occupancy(H, W, rng.uniform(0.3, 0.6), 300 + trial)
+        ids = np.zeros((H, W), np.uint32)
+        nz = np.flatnonzero(occ)
+        ids.reshape(-1)[nz] = rng.permutation(len(nz)).astype(np.uint32) + 1
+        tau = [rng.uniform(0.1, 2, size=(H, W)).astype(np.float32) for _ in range(2)]
+        p = O.make_params(model=model, n_per_side=1, band_cols=2, rho=0.05)
+        o = O.Oracle(W, H, p, 900 + trial, state={"occ": occ, "ids": ids, "tauA": tau[0],
+                                                  "tauB": tau[1]}, step=trial)
+        claims = {}
+        for yy, xx in zip(*np.nonzero(occ)):
+            i = o.decide_at(int(xx), int(yy))
+            if i == 0:
+                continue
+            s = 1 if occ[yy, xx] == 1 else -1
+            fx, fy = RE.FRAME[i]
+            tgt = (int(yy) + s * fy, int(xx) + s * fx)
+            claims[tgt] = claims.get(tgt, 0) + 1
+        o.step(1)
+        st = o.stats()
+        assert st["moved"] == len(claims), trial
+        assert st["conflicts"] == sum(1 for k in claims.values() if k >= 2), trial
+        k3_cells += sum(1 for k in claims.values() if k >= 3)
+    assert k3_cells >= 10, k3_cells
