@@ -78,11 +78,13 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "agent_step_aco_2048x2048_traffic.
 # tiled: proposals, resolution, step index; fused: one kernel + step index;
 # two-pass: two kernels + step index.
 VARIANTS = {"agent": lambda P: P.VARIANT_AGENT, "tiled": lambda P: P.VARIANT_TILED,
-            "fused": lambda P: P.VARIANT_FUSED, "two_pass": lambda P: P.VARIANT_TWO_PASS}
+            "fused": lambda P: P.VARIANT_FUSED, "two_pass": lambda P: P.VARIANT_TWO_PASS,
+            "deferred": lambda P: P.VARIANT_DEFERRED}
 KERNEL_NAMES = {"agent": "agent_stage1_kernel + agent_resolve_kernel",
                 "tiled": "propose_tile_kernel<16> + resolve_tile_kernel<16>",
                 "fused": "fused_step_kernel<64,16>",
-                "two_pass": "propose_plane_kernel + resolve_plane_kernel"}
+                "two_pass": "propose_plane_kernel + resolve_plane_kernel",
+                "deferred": "deferred_stage1_kernel + deferred_resolve_kernel"}
 
 
 def kernel_source_hash() -> str:

@@ -11,9 +11,13 @@
  * band_cols columns and heads for the left edge (-x).  Cells outside the grid
  * are never available.  One step (Sec. IV.b-d) is synchronous: every agent
  * reads the state at t and proposes a neighbouring empty cell (forward first,
- * else Eq. 1 for LEM or Eq. 2 for ACO); every empty cell then picks one of the
- * agents that chose it (scatter-to-gather, no atomics); pheromone evaporates
- * (Eq. 3) and the movers deposit into their own group's plane (Eq. 4, Eq. 5).
+ * else Eq. 1 for LEM or Eq. 2 for ACO); every empty cell then gathers the
+ * agents that chose it from its eight neighbours and picks one (Sec. IV.d:
+ * scatter turned into gather); pheromone evaporates (Eq. 3) and the movers
+ * deposit into their own group's plane (Eq. 4, Eq. 5).  The default step
+ * (PEDSIM_VARIANT_AGENT) resolves conflicts with no atomic operation; the
+ * tiled and fused variants combine one tile's claims in shared memory with an
+ * order-free bitwise OR.
  * Random numbers come from Philox4x64-10 keyed by (seed, cell, step, stream),
  * so results depend only on (W, H, params, seed, step count): not on the
  * stream, the launch shape, the tile shape or the batch a scenario runs in.
@@ -177,25 +181,41 @@ int sim_load(sim_t *s, const void *buf, size_t len);
  *                         with an agent in or next to them take the full
  *                         rule, the others only evaporate
  * PEDSIM_VARIANT_AGENT    (default) two kernels per step: one thread per agent
- *                         computes its proposal while the other CTAs of the
- *                         same kernel stream the pheromone evaporation of
- *                         most cells; then one thread per agent resolves its
- *                         target cell and applies the winner's move and
- *                         deposit, while further CTAs evaporate the remaining
- *                         cells (skipping the claimed ones, which their
- *                         winners write), and the last CTA advances the step
- *                         index
+ *                         computes its proposal (written at its own cell of a
+ *                         code plane) while the other CTAs of the same kernel
+ *                         stream the pheromone evaporation of most cells; then
+ *                         one thread per agent gathers its target's claimants
+ *                         from the codes of the target's neighbours and
+ *                         applies the winner's move and deposit, while
+ *                         further CTAs evaporate the remaining cells (skipping
+ *                         the claimed ones, which their winners write), and
+ *                         the last CTA advances the step index
+ * PEDSIM_VARIANT_DEFERRED the agent step without the dense evaporation
+ *                         stream (deferred evaporation): each cell keeps a
+ *                         one-byte stamp, the step at which its stored
+ *                         pheromone values are valid, and a value is brought
+ *                         up to date, by repeating Eq. 3's multiplication once
+ *                         per missed step, only where it is read (a blocked
+ *                         agent's available neighbours, a winner's target) and
+ *                         in a rolling refresh of 1/32 of the cells per step
+ *                         (no value is ever more than 32 steps old).  The same
+ *                         operations in the same order as evaporating every
+ *                         cell every step, so the results are identical; the
+ *                         dense traffic drops from 18 to 18/32 bytes per
+ *                         cell-step.  Read-back and checkpoints bring the
+ *                         planes up to the current step first.
  * Selecting a variant resets the tile shape to its default (tiled: 128 x 16;
- * fused: 64 x 16; the agent variant has none).                                */
+ * fused: 64 x 16; the agent and deferred variants have none).                */
 #define PEDSIM_VARIANT_TILED    0
 #define PEDSIM_VARIANT_TWO_PASS 1
 #define PEDSIM_VARIANT_FUSED    2
 #define PEDSIM_VARIANT_AGENT    3
+#define PEDSIM_VARIANT_DEFERRED 4
 int sim_set_variant(sim_t *s, int variant);
 
 /* Kernel launches that sim_step(s, 1) issues with the current variant into
- * *out (agent: 2; fused: 2; tiled and two-pass: 3, each counting the
- * step-index advance); PEDSIM_EINVAL for a null argument.                     */
+ * *out (agent and deferred: 2; fused: 2; tiled and two-pass: 3, each counting
+ * the step-index advance); PEDSIM_EINVAL for a null argument.                 */
 int sim_launches_per_step(sim_t *s, int *out);
 
 /* Tile shape of the current variant: tiled: tile_w = 128, tile_h in
@@ -208,6 +228,20 @@ int sim_set_tiling(sim_t *s, int tile_w, int tile_h, int ctas_per_sm);
 /* Sticky device error word of the handle: 0, or PEDSIM_ETIMEDOUT when a
  * bounded device wait gave up.  Synchronises the stream and clears it.       */
 int sim_device_status(sim_t *s);
+
+/* Failure-detection test hook (the paper has no counterpart: its single GPU
+ * run has no failure handling).  wait_cycles bounds every wait of the tiled
+ * variant (PEDSIM_VARIANT_TILED) on its TMA copies, in SM clock cycles
+ * (0 = the default, about 2 s at the maximum clock).  With test_flags =
+ * PEDSIM_TEST_SKIP_RESOLVE_LOADS the tiled resolution kernel issues none of
+ * its TMA loads, so its wait runs out: every CTA returns without writing any
+ * state, with nothing in flight, and the handle's device error word becomes
+ * PEDSIM_ETIMEDOUT (sim_device_status).  The state of the handle is then
+ * undefined (that step's resolution did not happen); destroy it.  No fault,
+ * trap or unbounded wait is involved, so the CUDA context stays usable.
+ * Takes effect from the next step; PEDSIM_EINVAL for unknown flags.           */
+#define PEDSIM_TEST_SKIP_RESOLVE_LOADS 1u
+int sim_set_wait_test(sim_t *s, uint64_t wait_cycles, uint32_t test_flags);
 
 void sim_destroy(sim_t *s);
 const char *sim_last_error(const sim_t *s);
@@ -230,8 +264,8 @@ int sim_batch_step(batch_t *b, int n);
 int sim_batch_stats(batch_t *b, int i, sim_stats_t *out);
 int sim_batch_read_grid(batch_t *b, int i, uint8_t *occ, uint32_t *ids, float *tauA,
                         float *tauB);
-/* Step variant (PEDSIM_VARIANT_TILED, _FUSED or _AGENT) and tile shape of
- * the batched launches (see sim_set_variant / sim_set_tiling).               */
+/* Step variant (PEDSIM_VARIANT_TILED, _FUSED, _AGENT or _DEFERRED) and tile
+ * shape of the batched launches (see sim_set_variant / sim_set_tiling).      */
 int sim_batch_set_variant(batch_t *b, int variant);
 int sim_batch_set_tiling(batch_t *b, int tile_w, int tile_h, int ctas_per_sm);
 int sim_batch_device_status(batch_t *b);

@@ -6,21 +6,22 @@
 //     proposal blocks     one thread per agent: forward first, else the full
 //                         rule (Eq. 1 LEM rank draw, Eq. 2 ACO roulette) from
 //                         the occupancy and pheromone at t; the direction code
-//                         goes to the agent's entry of `acode`, and its claim
-//                         bit (its scan offset seen from the target) is OR-ed
-//                         into the target's byte of the step's claim plane
+//                         goes to the agent's entry of `acode` and to its own
+//                         cell of the step's code plane
 //     stream blocks       every cell: both pheromone planes evaporated into
 //                         the planes of t+1 (Eq. 3); a pure 16-byte-vector
 //                         stream, the HBM-bound part of the step (ACO only)
 //   agent_resolve_kernel  one thread per agent with a proposal: the claim
-//                         mask of its target cell (all its claimants' bits),
-//                         the winner drawn from it as in Sec. IV.d, and the
-//                         winning agent moves: occupancy, id, position, tour
-//                         and arrival, and its deposit (Eq. 4/5) on top of the
-//                         evaporated value; beside the agent CTAs, stream CTAs
-//                         evaporate the step's last cell blocks (as many as
-//                         fill one resident wave), skipping the claimed cells,
-//                         whose winners write both planes
+//                         mask of its target cell gathered from the codes of
+//                         the target's eight neighbours (Sec. IV.d: scatter
+//                         turned into gather, no atomics), the winner drawn
+//                         from it, and the winning agent moves: occupancy,
+//                         id, position, tour and arrival, and its deposit
+//                         (Eq. 4/5) on top of the evaporated value; beside the
+//                         agent CTAs, stream CTAs evaporate the step's last
+//                         cell blocks (as many as fill one resident wave),
+//                         skipping the claimed cells (found from the same
+//                         codes), whose winners write both planes
 //
 // Occupancy lives in one plane, occ[0], updated in place: the proposals read
 // it (state at t) in the first kernel, the moves are applied to it only in
@@ -56,12 +57,15 @@ __device__ __forceinline__ int block_scenario(const uint32_t *__restrict__ prefi
     return lo;
 }
 
-// Proposal of agent index a (id a + 1) at step t.  The agent's code goes
-// to its per-agent byte, and its claim bit (scan offset 8 - code seen from
-// the target) is OR-ed into the target's byte of claim plane t & 1.  The
-// agent also clears, in the other plane (written next at step t + 1), the
-// byte of the target it claimed at step t - 1: that target is its cell now
-// if it moved, else its cell plus its previous direction.
+// Proposal of agent index a (id a + 1) at step t.  The agent's direction
+// code goes to its per-agent byte and to its own cell of code plane t & 1
+// (written every step, 0 for "stay"), where the resolution gathers it.  An
+// agent that moved during the previous step also clears its old cell in both
+// code planes: the plane of t - 1 holds its code of t - 1 there and the plane
+// of t may still hold its code of t - 2, and nobody else writes that cell
+// before step t + 1 (it was vacated at t - 1, so it is empty at t).  So at
+// every step the planes hold a nonzero code only at cells occupied at that
+// step.
 __device__ __forceinline__ void propose_agent(const ScenarioDesc &d, uint32_t a, uint64_t t)
 {
     const uint32_t id = a + 1u;
@@ -78,19 +82,13 @@ __device__ __forceinline__ void propose_agent(const ScenarioDesc &d, uint32_t a,
         x, y, g, W, H, (uint64_t)cell, t, d.seed, rp,
         [&](int dx, int dy) { return (int)__ldg(occ + ((int64_t)cell + (int64_t)dy * W + dx)); },
         tp ? tp + cell : nullptr, W);
-    const int pc = prev & 15;
-    if (pc) {
-        const int64_t old_target =
-            (prev & 0x80) ? (int64_t)cell : (int64_t)cell + (int64_t)kCodeDY[pc] * W + kCodeDX[pc];
-        d.claim[p ^ 1][old_target] = 0;
+    if (prev & 0x80) {
+        const int pc = prev & 15;
+        const int64_t old_cell = (int64_t)cell - ((int64_t)kCodeDY[pc] * W + kCodeDX[pc]);
+        d.codes[0][old_cell] = 0;
+        d.codes[1][old_cell] = 0;
     }
-    if (code) {
-        const int64_t target = (int64_t)cell + (int64_t)kCodeDY[code] * W + kCodeDX[code];
-        uint8_t *cb = d.claim[p] + target;
-        const uintptr_t addr = reinterpret_cast<uintptr_t>(cb);
-        atomicOr(reinterpret_cast<unsigned int *>(addr & ~(uintptr_t)3),
-                 (1u << (8 - code)) << (8 * (unsigned)(addr & 3)));
-    }
+    d.codes[p][cell] = (uint8_t)code;
     d.acode[id] = (uint8_t)(code | (g << 4));
 }
 
@@ -195,10 +193,67 @@ agent_stage1_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__re
     }
 }
 
-// Evaporation of cell block b in the resolution kernel, where the claims of
-// the step are final: the loads of the planes of t (which the first kernel
-// does not write) are issued before the wait for the first kernel, the
-// claim bytes after it, and claimed cells are left to their winners.
+// The codes a cell block's claim test reads, staged in shared memory: for
+// dy = -1, 0, 1, row dy + 1 holds the code plane's bytes c0 + dy * W - 1 ..
+// c0 + dy * W + kCellBlock (0 outside the plane), so cell c0 + k finds its
+// neighbour (dx, dy) at rows[dy + 1][k + 1 + dx].  Loaded with 8-byte
+// accesses by the whole CTA (cell blocks start at multiples of kCellBlock,
+// W is a multiple of 16, so every window start is 8-byte aligned after the
+// one-byte shift handled here).
+constexpr int kClaimRow = kCellBlock + 16;  // staged bytes per row (>= kCellBlock + 2)
+
+__device__ __forceinline__ void stage_claim_rows(uint8_t (*rows)[kClaimRow],
+                                                 const uint8_t *__restrict__ codes, size_t cells,
+                                                 int W, size_t c0)
+{
+    // rows[r][i] = codes[base_r - 8 + i], base_r = c0 + dy * W (i in 0 .. kClaimRow)
+    constexpr int kWords = kClaimRow / 8;
+    for (int i = threadIdx.x; i < 3 * kWords; i += kAgentBlock) {
+        const int r = i / kWords, w = i - r * kWords;
+        const int64_t start = (int64_t)c0 + (int64_t)(r - 1) * W - 8 + 8 * w;
+        uint2 v = make_uint2(0u, 0u);
+        if (start >= 0 && start + 8 <= (int64_t)cells)
+            v = __ldcg(reinterpret_cast<const uint2 *>(codes + start));
+        *reinterpret_cast<uint2 *>(&rows[r][8 * w]) = v;
+    }
+}
+
+// Claim flags of the four cells c0 + k .. c0 + k + 3 (k a multiple of 4, x
+// the column of the first): byte i of the result is nonzero when a neighbour
+// of cell c0 + k + i proposed it (gather: the claimant at offset (dx, dy)
+// from the cell holds the code of the move (-dx, -dy)).
+__device__ __forceinline__ uint32_t claimed4_staged(const uint8_t (*rows)[kClaimRow], int k, int x,
+                                                    int W)
+{
+    uint32_t hit = 0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        // bytes k+7 .. k+14 of the staged row are the cells k-1 .. k+6
+        const uint32_t w0 = *reinterpret_cast<const uint32_t *>(&rows[r][k + 4]);
+        const uint32_t w1 = *reinterpret_cast<const uint32_t *>(&rows[r][k + 8]);
+        const uint32_t w2 = *reinterpret_cast<const uint32_t *>(&rows[r][k + 12]);
+        uint32_t left = __byte_perm(w0, w1, 0x6543);   // cells k-1 .. k+2
+        const uint32_t mid = w1;                       // cells k   .. k+3
+        uint32_t right = __byte_perm(w1, w2, 0x4321);  // cells k+1 .. k+4
+        if (x == 0) left &= 0xFFFFFF00u;               // no left neighbour of column 0
+        if (x + 4 == W) right &= 0x00FFFFFFu;          // nor a right one of column W-1
+        const int dy = r - 1;
+        // codes of the moves into the cell from its left, same and right
+        // column of row dy: (+1, -dy), (0, -dy), (-1, -dy)
+        const uint32_t cl = dy < 0 ? 0x08080808u : dy == 0 ? 0x05050505u : 0x03030303u;
+        const uint32_t cc = dy < 0 ? 0x07070707u : 0x02020202u;
+        const uint32_t cr = dy < 0 ? 0x06060606u : dy == 0 ? 0x04040404u : 0x01010101u;
+        hit |= __vcmpeq4(left, cl) | __vcmpeq4(right, cr);
+        if (dy != 0) hit |= __vcmpeq4(mid, cc);
+    }
+    return hit;
+}
+
+// Evaporation of cell block b in the resolution kernel, where the proposals
+// of the step are final: the loads of the planes of t (which the first
+// kernel does not write) are issued before the wait for the first kernel,
+// the neighbours' codes after it, and claimed cells are left to their
+// winners.
 __device__ __forceinline__ void stream_block_claimed(const ScenarioDesc *__restrict__ descs,
                                                      const uint32_t *__restrict__ cell_prefix,
                                                      int n_scen, uint32_t b)
@@ -219,14 +274,19 @@ __device__ __forceinline__ void stream_block_claimed(const ScenarioDesc *__restr
             vb[k] = __ldcg(reinterpret_cast<const float4 *>(d.tau[1][p] + c));
         }
     }
-    pdl_wait();  // the claims of the step are in
+    pdl_wait();  // the proposals of the step are in
     pdl_trigger();
     if (!active) return;
+    const int W = d.W;
+    __shared__ __align__(16) uint8_t rows[3][kClaimRow];
+    stage_claim_rows(rows, d.codes[p], cells, W, c0);
+    __syncthreads();
     uint32_t cw[kStreamVec];
 #pragma unroll
     for (int k = 0; k < kStreamVec; ++k) {
         const size_t c = c0 + 4 * ((size_t)k * kAgentBlock + threadIdx.x);
-        cw[k] = c < cells ? __ldcg(reinterpret_cast<const unsigned int *>(d.claim[p] + c)) : 0u;
+        const int kk = 4 * (k * kAgentBlock + (int)threadIdx.x);
+        cw[k] = c < cells ? claimed4_staged(rows, kk, (int)(c % (size_t)W), W) : 0u;
     }
     const float q = d.q;
     float *const na = d.tau[0][p ^ 1], *const nb = d.tau[1][p ^ 1];
@@ -256,7 +316,7 @@ __device__ __forceinline__ void stream_block_claimed(const ScenarioDesc *__restr
 
 // Resolution work of one agent: its own entries (position, tour and arrival
 // before the wait for the first kernel, its code after it) and its target's
-// claim mask and pheromone (a second round).  Nothing read here is written
+// neighbours' codes and pheromone (a second round).  Nothing read here is written
 // by the resolution kernel before it is read (position and per-agent entries
 // only by their own thread, after reading), and the rounds of several agents
 // overlap.
@@ -291,21 +351,42 @@ __device__ __forceinline__ void resolve_load_code(const ScenarioDesc &d, Resolve
     r.g = ac >> 4;
 }
 
-// Claim mask of the target (bit j: its claimant at scan offset j; every
-// claimant's proposal pass has OR-ed its bit in) and the target's own-group
-// pheromone at t.
+// Claim mask of target cell (tx, ty), gathered from its eight neighbours'
+// codes in the step's code plane (bit j: the neighbour at scan offset j
+// proposed the target, i.e. holds code 8 - j; no atomics, Sec. IV.d).
+// cp points at the target's byte of the plane.
+__device__ __forceinline__ uint32_t gather_claims(const uint8_t *cp, int W, int H, int tx, int ty)
+{
+    int v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        // scan offset j: (-1,-1) (0,-1) (1,-1) (-1,0) (1,0) (-1,1) (0,1) (1,1)
+        const int ox = j < 3 ? j - 1 : j < 5 ? 2 * j - 7 : j - 6;
+        const int oy = j < 3 ? -1 : j < 5 ? 0 : 1;
+        const bool inside = (unsigned)(tx + ox) < (unsigned)W && (unsigned)(ty + oy) < (unsigned)H;
+        v[j] = inside ? (int)__ldg(cp + (int64_t)oy * W + ox) : 0;
+    }
+    uint32_t m = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) m |= (v[j] == 8 - j ? 1u : 0u) << j;
+    return m;
+}
+
+// The target's claim mask and its own-group pheromone at t.
 // late_from: the scenario's first cell block evaporated in the resolution
 // kernel (its cell blocks from there on skip claimed cells).
 __device__ __forceinline__ void resolve_load_target(const ScenarioDesc &d, uint64_t t, Resolve &r,
                                                     uint32_t late_from)
 {
-    const int W = d.W;
+    const int W = d.W, H = d.H;
     const int p = (int)(t & 1);
-    r.target = (int64_t)r.cell + (int64_t)kCodeDY[r.code] * W + kCodeDX[r.code];
+    const int dx = kCodeDX[r.code], dy = kCodeDY[r.code];
+    r.target = (int64_t)r.cell + (int64_t)dy * W + dx;
+    const int tx = (int)(r.cell % (uint32_t)W) + dx, ty = (int)(r.cell / (uint32_t)W) + dy;
     r.late = (uint64_t)r.target / kCellBlock >= late_from;
     r.tau_t = d.model == 1 ? __ldg(d.tau[r.g == 2 ? 1 : 0][p] + r.target) : 0.0f;
     r.tau_o = d.model == 1 && r.late ? __ldg(d.tau[r.g == 2 ? 0 : 1][p] + r.target) : 0.0f;
-    r.mask = __ldg(d.claim[p] + r.target);
+    r.mask = gather_claims(d.codes[p] + r.target, W, H, tx, ty);
 }
 
 // The winner of the target (Sec. IV.d) and, if it is this agent, its move.
@@ -354,7 +435,10 @@ __device__ __forceinline__ void resolve_apply(const ScenarioDesc &d, uint64_t t,
 // and 4 were measured slower at 2048^2 and 8192^2).
 constexpr int kResolveBlocks = 1;  // the resolution kernel's CTA indices assume 1
 
-__global__ void __launch_bounds__(kAgentBlock)
+// Five resident CTAs per SM (48 registers): the gathered claim mask alone
+// would take the compiler to 54 registers and four CTAs per SM, a smaller
+// resident wave for the late cell blocks.
+__global__ void __launch_bounds__(kAgentBlock, 5)
 agent_resolve_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__restrict__ agent_prefix,
                      const uint32_t *__restrict__ cell_prefix, int n_scen, uint32_t agent_blocks,
                      uint32_t first_late, uint32_t late_blocks, ActivityCtl *__restrict__ ctl)
@@ -447,6 +531,292 @@ agent_resolve_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__r
 }
 
 
+// ---------------------------------------------------------------------------
+// Deferred evaporation (PEDSIM_VARIANT_DEFERRED): the same agent-parallel
+// step without the dense stream.  Each scenario keeps one pheromone plane per
+// group, updated in place, and one byte per cell, the stamp: the low byte of
+// the step at which the cell's two stored values are valid.  The value at a
+// later step t is the stored value evaporated once per missed step, i.e.
+// fl(v * q) applied (t - stamp) mod 256 times -- the very operations Eq. 3
+// performs on the cell, in the same order -- so every value read, deposited
+// on or copied out equals the every-step evaporation bit for bit.  A value
+// is brought up to date only where it is read (the blocked agents' available
+// neighbours, each winner's target) and, so that no value is ever more than
+// kDeferPeriod steps old, in a rolling refresh: at step t the resolution
+// kernel brings the cell blocks b with b = t (mod kDeferPeriod) up to step
+// t + 1.  The dense traffic is then that of one full pass every
+// kDeferPeriod steps: 18 / kDeferPeriod bytes per cell-step.
+// ---------------------------------------------------------------------------
+#ifndef PEDSIM_DEFER_PERIOD
+#define PEDSIM_DEFER_PERIOD 32
+#endif
+constexpr uint32_t kDeferPeriod = PEDSIM_DEFER_PERIOD;
+static_assert(kDeferPeriod >= 1 && kDeferPeriod <= 128, "stamp ages must stay below 256");
+
+// v evaporated `age` times (Eq. 3 once per step).
+__device__ __forceinline__ float evaporate_n(float v, uint32_t age, float q)
+{
+    for (uint32_t i = 0; i < age; ++i) v = __fmul_rn(v, q);
+    return v;
+}
+
+// Own-group pheromone at step `now` at offset (dx, dy) from an agent: value
+// and stamp at that cell, brought up to date.
+struct DeferredTau {
+    const float *v;
+    const uint8_t *stamp;
+    int stride;
+    uint32_t now;
+    float q;
+    __device__ __forceinline__ float operator()(int dx, int dy) const
+    {
+        const int off = dy * stride + dx;
+        return evaporate_n(__ldg(v + off), (now - (uint32_t)__ldg(stamp + off)) & 255u, q);
+    }
+};
+
+// Proposal of agent index a at step t (as propose_agent; the pheromone of
+// the blocked path is read through the stamps).
+__device__ __forceinline__ void propose_agent_deferred(const ScenarioDesc &d, uint32_t a, uint64_t t)
+{
+    const uint32_t id = a + 1u;
+    const int W = d.W, H = d.H;
+    const uint32_t cell = __ldg(d.pos + id);
+    const int prev = __ldg(d.acode + id);
+    const int x = (int)(cell % (uint32_t)W), y = (int)(cell / (uint32_t)W);
+    const int p = (int)(t & 1);
+    const uint8_t *occ = d.occ[0];
+    const int g = __ldg(occ + cell);
+    const RuleParams rp{d.model, d.alpha, d.beta, d.lem_scale};
+    const float *tp = d.tau[g == 2 ? 1 : 0][0];
+    const auto occ_at = [&](int dx, int dy) {
+        return (int)__ldg(occ + ((int64_t)cell + (int64_t)dy * W + dx));
+    };
+    const int code =
+        tp ? propose_with(x, y, g, W, H, (uint64_t)cell, t, d.seed, rp, occ_at,
+                          DeferredTau{tp + cell, d.stamp + cell, W, (uint32_t)t, d.q})
+           : propose(x, y, g, W, H, (uint64_t)cell, t, d.seed, rp, occ_at, nullptr, W);
+    if (prev & 0x80) {
+        const int pc = prev & 15;
+        const int64_t old_cell = (int64_t)cell - ((int64_t)kCodeDY[pc] * W + kCodeDX[pc]);
+        d.codes[0][old_cell] = 0;
+        d.codes[1][old_cell] = 0;
+    }
+    d.codes[p][cell] = (uint8_t)code;
+    d.acode[id] = (uint8_t)(code | (g << 4));
+}
+
+// First kernel of the deferred step: the proposals only.
+__global__ void __launch_bounds__(kAgentBlock)
+deferred_stage1_kernel(const ScenarioDesc *__restrict__ descs,
+                       const uint32_t *__restrict__ agent_prefix, int n_scen, uint32_t agent_blocks)
+{
+    pdl_wait();
+    pdl_trigger();
+    const uint32_t b = blockIdx.x;
+    if (b >= agent_blocks) return;
+    const int s = block_scenario(agent_prefix, n_scen, b);
+    const ScenarioDesc &d = descs[s];
+    const uint64_t t = d.step;
+    const uint32_t a = (b - __ldg(agent_prefix + s)) * kAgentBlock + threadIdx.x;
+    if (t < d.end_step && a < 2u * d.n_per_side) propose_agent_deferred(d, a, t);
+}
+
+// Rolling refresh of cell block b of scenario d at step t: every unclaimed
+// cell is brought up to step t + 1 (its stamp becomes t + 1); claimed cells
+// are left to their winners, which write both planes and the stamp.  The
+// values and stamps (not written by the first kernel) are loaded before the
+// wait for it, the neighbours' codes after it.
+__device__ __forceinline__ void refresh_block(const ScenarioDesc &d, uint64_t t, uint32_t b)
+{
+    const size_t cells = (size_t)d.W * (size_t)d.H;
+    const size_t c0 = (size_t)b * kCellBlock;
+    float4 va[kStreamVec], vb[kStreamVec];
+    uint32_t sw[kStreamVec];
+#pragma unroll
+    for (int k = 0; k < kStreamVec; ++k) {
+        const size_t c = c0 + 4 * ((size_t)k * kAgentBlock + threadIdx.x);
+        if (c < cells) {
+            va[k] = __ldcg(reinterpret_cast<const float4 *>(d.tau[0][0] + c));
+            vb[k] = __ldcg(reinterpret_cast<const float4 *>(d.tau[1][0] + c));
+            sw[k] = __ldcg(reinterpret_cast<const unsigned int *>(d.stamp + c));
+        }
+    }
+    pdl_wait();  // the proposals of the step are in
+    pdl_trigger();
+    const int W = d.W, p = (int)(t & 1);
+    const uint32_t now = (uint32_t)t, next = (uint32_t)(t + 1) & 255u;
+    const float q = d.q;
+    __shared__ __align__(16) uint8_t rows[3][kClaimRow];
+    stage_claim_rows(rows, d.codes[p], cells, W, c0);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kStreamVec; ++k) {
+        const size_t c = c0 + 4 * ((size_t)k * kAgentBlock + threadIdx.x);
+        if (c >= cells) continue;
+        const uint32_t cw =
+            claimed4_staged(rows, 4 * (k * kAgentBlock + (int)threadIdx.x), (int)(c % (size_t)W), W);
+        float a_[4] = {va[k].x, va[k].y, va[k].z, va[k].w};
+        float b_[4] = {vb[k].x, vb[k].y, vb[k].z, vb[k].w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t age = ((now - (sw[k] >> (8 * j))) & 255u) + 1u;
+            a_[j] = evaporate_n(a_[j], age, q);
+            b_[j] = evaporate_n(b_[j], age, q);
+        }
+        if (cw == 0u) {
+            *reinterpret_cast<float4 *>(d.tau[0][0] + c) = make_float4(a_[0], a_[1], a_[2], a_[3]);
+            *reinterpret_cast<float4 *>(d.tau[1][0] + c) = make_float4(b_[0], b_[1], b_[2], b_[3]);
+            *reinterpret_cast<unsigned int *>(d.stamp + c) = next * 0x01010101u;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if ((cw >> (8 * j)) & 0xffu) continue;  // the winner writes this cell
+                d.tau[0][0][c + j] = a_[j];
+                d.tau[1][0][c + j] = b_[j];
+                d.stamp[c + j] = (uint8_t)next;
+            }
+        }
+    }
+}
+
+// Second kernel of the deferred step.  CTAs 0 .. agent_blocks-1 resolve one
+// agent per thread as agent_resolve_kernel does; a winner brings both of its
+// target's values up to step t, then writes the other group's evaporated
+// value, its own group's evaporated value plus the deposit (Eq. 4/5) and the
+// stamp t + 1.  The CTAs after them refresh the step's slice of cell blocks:
+// CTA j of scenario s (slice_prefix) takes block j * kDeferPeriod + t mod
+// kDeferPeriod.  The CTA holding the last ticket advances the step indices.
+__global__ void __launch_bounds__(kAgentBlock, 5)
+deferred_resolve_kernel(const ScenarioDesc *__restrict__ descs,
+                        const uint32_t *__restrict__ agent_prefix,
+                        const uint32_t *__restrict__ cell_prefix,
+                        const uint32_t *__restrict__ slice_prefix, int n_scen,
+                        uint32_t agent_blocks, ActivityCtl *__restrict__ ctl)
+{
+    unsigned int ticket = 0;
+    if (blockIdx.x >= agent_blocks) {
+        const uint32_t j = blockIdx.x - agent_blocks;
+        const int s = block_scenario(slice_prefix, n_scen, j);
+        const ScenarioDesc &d = descs[s];
+        const uint64_t t = d.step;
+        const uint32_t b = (j - __ldg(slice_prefix + s)) * kDeferPeriod +
+                           (uint32_t)(t % kDeferPeriod);
+        const uint32_t blocks = __ldg(cell_prefix + s + 1) - __ldg(cell_prefix + s);
+        if (t < d.end_step && b < blocks) {
+            refresh_block(d, t, b);
+        } else {
+            pdl_wait();
+            pdl_trigger();
+        }
+        __syncthreads();  // every thread has read the step index
+        if (threadIdx.x == 0) ticket = atomicAdd(&ctl->ticket, 1u);
+    } else {
+        const uint32_t bb = blockIdx.x;
+        const int s = block_scenario(agent_prefix, n_scen, bb);
+        const ScenarioDesc &d = descs[s];
+        const uint32_t lb = bb - __ldg(agent_prefix + s);
+        const uint64_t t = d.step;
+        const uint32_t a = lb * kAgentBlock + threadIdx.x;
+        bool live = t < d.end_step && a < 2u * d.n_per_side;
+        Resolve r;
+        if (live) resolve_load_own(d, a, r);
+        pdl_wait();  // proposals complete
+        pdl_trigger();
+        if (live) {
+            resolve_load_code(d, r);
+            live = r.code != 0;
+        }
+        __syncthreads();  // every thread has read the step index
+        if (threadIdx.x == 0) ticket = atomicAdd(&ctl->ticket, 1u);
+        Counts cnt;
+        if (live) {
+            // the target's neighbours' codes, values and stamp (one round)
+            const int W = d.W, H = d.H;
+            const int dx = kCodeDX[r.code], dy = kCodeDY[r.code];
+            r.target = (int64_t)r.cell + (int64_t)dy * W + dx;
+            const int tx = (int)(r.cell % (uint32_t)W) + dx;
+            const bool aco = d.model == 1;
+            float vt = 0.0f, vo = 0.0f;
+            uint32_t age = 0;
+            if (aco) {
+                vt = __ldg(d.tau[r.g == 2 ? 1 : 0][0] + r.target);
+                vo = __ldg(d.tau[r.g == 2 ? 0 : 1][0] + r.target);
+                age = ((uint32_t)t - (uint32_t)__ldg(d.stamp + r.target)) & 255u;
+            }
+            r.mask = gather_claims(d.codes[(int)(t & 1)] + r.target, W, H, tx,
+                                   (int)(r.cell / (uint32_t)W) + dy);
+            const uint32_t k = (uint32_t)__popc(r.mask);
+            const uint32_t mine = 8u - (uint32_t)r.code;
+            const uint32_t win =
+                k == 1 ? mine : pick_claimant(r.mask, k, (uint64_t)r.target, t, d.seed);
+            if (win == mine) {
+                const int g = r.g;
+                const int tx = (int)(r.cell % (uint32_t)W) + dx;
+                d.occ[0][r.target] = (uint8_t)g;
+                d.occ[0][r.cell] = 0;
+                d.pos[r.id] = (uint32_t)r.target;
+                d.acode[r.id] = (uint8_t)(r.code | (g << 4) | 0x80);
+                d.ids[r.target] = r.id;
+                float dep = d.deposit;
+                if (aco && d.deposit_mode == 1) {
+                    const float L = __fadd_rn(r.tour0, (dx != 0 && dy != 0) ? kSqrt2 : 1.0f);
+                    d.tour[r.id] = L;
+                    dep = __fdiv_rn(1.0f, L);
+                }
+                const bool in_band = g == 1 ? tx >= W - (int)d.band : tx < (int)d.band;
+                if (in_band && r.arrived == 0) {
+                    d.arrival[r.id] = (uint32_t)(t + 1);
+                    if (g == 1) ++cnt.crossed_a; else ++cnt.crossed_b;
+                }
+                if (aco) {
+                    const float q = d.q;
+                    // values at t, then step t's evaporation and the deposit
+                    vt = __fmul_rn(evaporate_n(vt, age, q), q);
+                    vo = __fmul_rn(evaporate_n(vo, age, q), q);
+                    d.tau[g == 2 ? 1 : 0][0][r.target] = __fadd_rn(vt, dep);
+                    d.tau[g == 2 ? 0 : 1][0][r.target] = vo;
+                    d.stamp[r.target] = (uint8_t)(t + 1);
+                }
+                ++cnt.moved;
+                if (k >= 2) ++cnt.conflicts;
+            }
+        }
+        flush_counts(d, cnt, lb % d.n_slots);
+    }
+    if (threadIdx.x < 32) {
+        const bool last = __shfl_sync(0xffffffffu, ticket == gridDim.x - 1, 0);
+        if (last) {
+            ScenarioDesc *md = const_cast<ScenarioDesc *>(descs);
+            for (int i = threadIdx.x; i < n_scen; i += 32) {
+                const unsigned long long v = md[i].step;
+                if (v < md[i].end_step) md[i].step = v + 1;
+            }
+            if (threadIdx.x == 0) ctl->ticket = 0u;
+        }
+    }
+}
+
+// Brings every cell of one scenario up to its current step (both planes,
+// stamps := step): read-back, checkpoints and a change of step variant see
+// plain planes.  Values do not change, only how old their stored form is.
+__global__ void deferred_catch_up_kernel(const ScenarioDesc *__restrict__ dp)
+{
+    const ScenarioDesc &d = *dp;
+    if (d.model != 1) return;
+    const size_t cells = (size_t)d.W * (size_t)d.H;
+    const uint32_t now = (uint32_t)d.step;
+    const float q = d.q;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells; c += stride) {
+        const uint32_t age = (now - (uint32_t)d.stamp[c]) & 255u;
+        if (!age) continue;
+        d.tau[0][0][c] = evaporate_n(d.tau[0][0][c], age, q);
+        d.tau[1][0][c] = evaporate_n(d.tau[1][0][c], age, q);
+        d.stamp[c] = (uint8_t)now;
+    }
+}
+
 __global__ void build_pos_kernel(const ScenarioDesc *__restrict__ dp, int plane)
 {
     const ScenarioDesc &d = *dp;
@@ -454,8 +824,8 @@ __global__ void build_pos_kernel(const ScenarioDesc *__restrict__ dp, int plane)
     const uint8_t *occ = d.occ[plane];
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells; c += stride) {
-        d.claim[0][c] = 0;
-        d.claim[1][c] = 0;
+        d.codes[0][c] = 0;
+        d.codes[1][c] = 0;
         if (occ[c]) d.pos[d.ids[c]] = (uint32_t)c;
     }
     const size_t agents = 2 * (size_t)d.n_per_side + 1;
@@ -537,6 +907,37 @@ cudaError_t launch_agent_step(const ScenarioDesc *d_descs, const uint32_t *d_cel
     return launch_pdl(agent_resolve_kernel, g, (unsigned)kAgentBlock, stream, d_descs,
                       d_agent_prefix, d_cell_prefix, n, agent_blocks, cell_blocks - late, late,
                       ctl);
+}
+
+cudaError_t launch_deferred_step(const ScenarioDesc *d_descs, const uint32_t *d_cell_prefix,
+                                 const uint32_t *d_agent_prefix, const uint32_t *d_slice_prefix,
+                                 int n, uint32_t slices, uint32_t agent_blocks, ActivityCtl *ctl,
+                                 cudaStream_t stream)
+{
+    if (n <= 0) return cudaSuccess;
+    // the first kernel runs even with no agent: the refresh CTAs' loads
+    // before their wait rely on it having waited for the previous step
+    cudaError_t e = launch_pdl(deferred_stage1_kernel, agent_blocks > 0 ? agent_blocks : 1u,
+                               (unsigned)kAgentBlock, stream, d_descs, d_agent_prefix, n,
+                               agent_blocks);
+    if (e != cudaSuccess) return e;
+    const uint32_t g = agent_blocks + slices > 0 ? agent_blocks + slices : 1u;
+    return launch_pdl(deferred_resolve_kernel, g, (unsigned)kAgentBlock, stream, d_descs,
+                      d_agent_prefix, d_cell_prefix, d_slice_prefix, n, agent_blocks, ctl);
+}
+
+uint32_t deferred_slices(uint32_t cell_blocks)
+{
+    return (cell_blocks + kDeferPeriod - 1) / kDeferPeriod;
+}
+
+cudaError_t launch_deferred_catch_up(const ScenarioDesc *d_desc, int cells, cudaStream_t stream)
+{
+    int blocks = (cells + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    if (blocks < 1) blocks = 1;
+    deferred_catch_up_kernel<<<blocks, 256, 0, stream>>>(d_desc);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_build_pos(const ScenarioDesc *d_desc, int cells, int plane, cudaStream_t stream)

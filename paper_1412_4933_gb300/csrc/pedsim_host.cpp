@@ -24,7 +24,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // Device memory layout of one scenario (one allocation)
 // ---------------------------------------------------------------------------
 struct Layout {
-    size_t desc, occ[2], prop, claim, ids, tau[2][2], arrival, tour, pos, acode, part, error,
+    size_t desc, occ[2], prop, codes, ids, tau[2][2], stamp, arrival, tour, pos, acode, part, error,
         prefix, counts, totals, act, act_bytes;
     size_t total;
     uint32_t n_slots;
@@ -70,17 +70,18 @@ Layout make_layout(int W, int H, const sim_params &p)
     L.occ[0] = take(cells);
     L.occ[1] = take(cells);
     L.prop = take(cells);  // proposal plane of the two-kernel step variants
-    L.claim = take(2 * cells);  // claim-mask planes of the agent-parallel variant
+    L.codes = take(2 * cells);  // code planes of the agent-parallel variant
     L.ids = take(4 * cells);
     for (int g = 0; g < 2; ++g)
         for (int q = 0; q < 2; ++q) L.tau[g][q] = L.has_tau ? take(4 * cells) : 0;
+    L.stamp = L.has_tau ? take(cells) : 0;  // deferred-evaporation stamps
     L.arrival = take(4 * agents);
     L.tour = L.has_tour ? take(4 * agents) : 0;
     L.pos = take(4 * agents);  // cell of each agent (agent-parallel variant)
     L.acode = take(agents);    // proposal code and group of each agent (same)
     L.part = take(8 * kNumCounters * (size_t)L.n_slots);
     L.error = take(4);
-    L.prefix = take(3 * 8);  // tile, cell-block and agent-block prefixes of one scenario
+    L.prefix = take(4 * 8);  // tile, cell-block, agent-block and refresh-slice prefixes
     L.counts = take(4 * kGridCounts);
     L.totals = take(8 * kNumCounters);
     // tile-activity block of the fused step, sized for its smallest tiles
@@ -170,6 +171,8 @@ struct sim_s {
     int sms = 1;
     cudaGraphExec_t graph = nullptr;
     cudaStream_t graph_stream = nullptr;
+    unsigned long long wait_cycles = 0;  // bounded-wait limit of the tiled variant (0 = default)
+    uint32_t test_flags = 0;             // failure-detection test hook
     std::string err;
 };
 
@@ -223,12 +226,13 @@ int upload_desc(sim_t *s)
     d.occ[0] = m + L.occ[0];
     d.occ[1] = m + L.occ[1];
     d.prop = m + L.prop;
-    d.claim[0] = m + L.claim;
-    d.claim[1] = m + L.claim + (size_t)s->W * (size_t)s->H;
+    d.codes[0] = m + L.codes;
+    d.codes[1] = m + L.codes + (size_t)s->W * (size_t)s->H;
     d.ids = reinterpret_cast<uint32_t *>(m + L.ids);
     for (int g = 0; g < 2; ++g)
         for (int q = 0; q < 2; ++q)
             d.tau[g][q] = L.has_tau ? reinterpret_cast<float *>(m + L.tau[g][q]) : nullptr;
+    d.stamp = L.has_tau ? m + L.stamp : nullptr;
     d.arrival = reinterpret_cast<uint32_t *>(m + L.arrival);
     d.tour = L.has_tour ? reinterpret_cast<float *>(m + L.tour) : nullptr;
     d.pos = reinterpret_cast<uint32_t *>(m + L.pos);
@@ -255,6 +259,8 @@ int upload_desc(sim_t *s)
     d.deposit = s->p.deposit;
     d.lem_scale = 0x1p-16f / s->p.lem_sigma;
     d.tau0 = s->p.tau0;
+    d.wait_cycles = s->wait_cycles;
+    d.test_flags = s->test_flags;
     const int TWd = s->tile_w, THd = s->tile_h;
     if (s->variant == kVariantFused) {
         for (int q = 0; q < 2; ++q)
@@ -288,8 +294,9 @@ int upload_desc(sim_t *s)
                                          d.tau[g][q], s->W, s->H, TWd, THd);
         if (!ok) return fail(s, PEDSIM_ECUDA, "cuTensorMapEncodeTiled failed (tiled variant)");
     }
-    const uint32_t prefix[6] = {0u, (uint32_t)(d.tiles_x * d.tiles_y), 0u,
-                                cell_blocks(s->W, s->H, s->p), 0u, agent_blocks(s->p.n_per_side)};
+    const uint32_t cb = cell_blocks(s->W, s->H, s->p);
+    const uint32_t prefix[8] = {0u, (uint32_t)(d.tiles_x * d.tiles_y), 0u, cb,
+                                0u, agent_blocks(s->p.n_per_side), 0u, deferred_slices(cb)};
     // the handle's own descriptor becomes the live one again (a work list that
     // held it re-uploads its copy when it runs next)
     s->d_desc = s->own_desc;
@@ -302,6 +309,11 @@ int upload_desc(sim_t *s)
     drop_graph(s);
     return PEDSIM_OK;
 }
+
+// The agent-parallel and deferred steps advance the device step index
+// themselves (no launch_advance), keep their occupancy in plane 0 updated in
+// place and need the per-agent positions.
+bool self_advancing(int variant) { return variant == kVariantAgent || variant == kVariantDeferred; }
 
 int fused_grid(const sim_t *s, uint32_t total)
 {
@@ -329,6 +341,13 @@ int launch_one_step(sim_t *s, int t_off, cudaStream_t st)
                                       s->d_act, st));
         return PEDSIM_OK;
     }
+    if (s->variant == kVariantDeferred) {
+        SIM_CUDA(s, launch_deferred_step(s->d_desc, s->d_prefix + 2, s->d_prefix + 4,
+                                         s->d_prefix + 6, 1,
+                                         deferred_slices(cell_blocks(s->W, s->H, s->p)),
+                                         agent_blocks(s->p.n_per_side), s->d_act, st));
+        return PEDSIM_OK;
+    }
     SIM_CUDA(s, launch_fused_step(s->d_desc, s->d_prefix, 1, total, t_off, s->tile_w, s->tile_h,
                                   fused_grid(s, total), s->d_act, st));
     return PEDSIM_OK;
@@ -342,7 +361,7 @@ int ensure_graph(sim_t *s)
     SIM_CUDA(s, cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
     int rc = PEDSIM_OK;
     for (int k = 0; k < kGraphSteps && rc == PEDSIM_OK; ++k) rc = launch_one_step(s, k, s->cap);
-    if (rc == PEDSIM_OK && s->variant != kVariantAgent) {
+    if (rc == PEDSIM_OK && !self_advancing(s->variant)) {
         cudaError_t ea = launch_advance(s->d_desc, 1, kGraphSteps, s->cap);
         if (ea != cudaSuccess) rc = cuda_fail(s, ea, "advance kernel capture");
     }
@@ -387,7 +406,13 @@ size_t agents_len(const sim_t *s) { return 2 * (size_t)s->p.n_per_side + 1; }
 int occ_plane(const sim_t *s, int variant, unsigned long long step)
 {
     (void)s;
-    return variant == kVariantAgent ? 0 : (int)(step & 1);
+    return self_advancing(variant) ? 0 : (int)(step & 1);
+}
+// Pheromone plane that holds the current state: the deferred variant keeps
+// one plane per group (plane 0, with per-cell stamps), the others alternate.
+int tau_plane(int variant, unsigned long long step)
+{
+    return variant == kVariantDeferred ? 0 : (int)(step & 1);
 }
 int occ_plane(const sim_t *s) { return occ_plane(s, s->variant, s->step); }
 
@@ -410,18 +435,30 @@ int resync_step(sim_t *s)
 // that variant keeps them up to date).
 int switch_variant(sim_t *s, int variant, int tw, int th, int cps)
 {
+    const size_t cells = (size_t)s->W * (size_t)s->H;
     const int from = occ_plane(s), to = occ_plane(s, variant, s->step);
     if (from != to)
-        SIM_CUDA(s, cudaMemcpyAsync(s->hdesc.occ[to], s->hdesc.occ[from],
-                                    (size_t)s->W * (size_t)s->H, cudaMemcpyDeviceToDevice,
-                                    s->stream));
+        SIM_CUDA(s, cudaMemcpyAsync(s->hdesc.occ[to], s->hdesc.occ[from], cells,
+                                    cudaMemcpyDeviceToDevice, s->stream));
     const int old = s->variant;
+    if (s->L.has_tau) {
+        // pheromone: deferred planes are brought up to the step first, then
+        // the state moves to the plane the new variant keeps it in
+        if (old == kVariantDeferred) SIM_CUDA(s, launch_deferred_catch_up(s->d_desc, (int)cells, s->stream));
+        const int tf = tau_plane(old, s->step), tt = tau_plane(variant, s->step);
+        if (tf != tt)
+            for (int g = 0; g < 2; ++g)
+                SIM_CUDA(s, cudaMemcpyAsync(s->hdesc.tau[g][tt], s->hdesc.tau[g][tf], 4 * cells,
+                                            cudaMemcpyDeviceToDevice, s->stream));
+        if (variant == kVariantDeferred && old != kVariantDeferred)
+            SIM_CUDA(s, cudaMemsetAsync(s->hdesc.stamp, (int)(s->step & 255u), cells, s->stream));
+    }
     s->variant = variant;
     s->tile_w = tw;
     s->tile_h = th;
     s->ctas_per_sm = cps;
     int rc = upload_desc(s);
-    if (rc == PEDSIM_OK && variant == kVariantAgent && old != kVariantAgent)
+    if (rc == PEDSIM_OK && self_advancing(variant) && !self_advancing(old))
         SIM_CUDA(s, launch_build_pos(s->d_desc, s->W * s->H, to, s->stream));
     return rc;
 }
@@ -542,7 +579,7 @@ int sim_step(sim_t *s, int n)
             int rc = launch_one_step(s, k, s->stream);
             if (rc != PEDSIM_OK) return rc;
         }
-        if (s->variant != kVariantAgent)
+        if (!self_advancing(s->variant))
             SIM_CUDA(s, launch_advance(s->d_desc, 1, rem, s->stream));
     }
     s->step += (unsigned long long)n;
@@ -568,9 +605,12 @@ int sim_read_grid(sim_t *s, uint8_t *occ, uint32_t *ids, float *tauA, float *tau
     if (ids)
         SIM_CUDA(s, cudaMemcpyAsync(ids, s->hdesc.ids, 4 * cells, cudaMemcpyDeviceToHost, s->stream));
     float *dst[2] = {tauA, tauB};
+    const int tpl = s->variant == kVariantDeferred ? 0 : par;
+    if (s->variant == kVariantDeferred && s->L.has_tau && (tauA || tauB))
+        SIM_CUDA(s, launch_deferred_catch_up(s->d_desc, (int)cells, s->stream));
     for (int g = 0; g < 2; ++g) {
         if (!dst[g] || !s->L.has_tau) continue;
-        SIM_CUDA(s, cudaMemcpyAsync(dst[g], s->hdesc.tau[g][par], 4 * cells, cudaMemcpyDeviceToHost,
+        SIM_CUDA(s, cudaMemcpyAsync(dst[g], s->hdesc.tau[g][tpl], 4 * cells, cudaMemcpyDeviceToHost,
                                     s->stream));
     }
     SIM_CUDA(s, cudaStreamSynchronize(s->stream));
@@ -624,12 +664,14 @@ int sim_set_state(sim_t *s, uint64_t seed, uint64_t step, const uint8_t *occ, co
                                 s->stream));
     SIM_CUDA(s, cudaMemcpyAsync(s->hdesc.ids, ids, 4 * cells, cudaMemcpyHostToDevice, s->stream));
     if (s->L.has_tau) {
+        // (init filled plane 0 with tau0 and the stamps with the step index)
+        const int tpl = tau_plane(s->variant, step);
         const float *src[2] = {tauA, tauB};
         for (int g = 0; g < 2; ++g)
             if (src[g])
-                SIM_CUDA(s, cudaMemcpyAsync(s->hdesc.tau[g][par], src[g], 4 * cells,
+                SIM_CUDA(s, cudaMemcpyAsync(s->hdesc.tau[g][tpl], src[g], 4 * cells,
                                             cudaMemcpyHostToDevice, s->stream));
-            else if (par == 1)
+            else if (tpl == 1)
                 SIM_CUDA(s, cudaMemcpyAsync(s->hdesc.tau[g][1], s->hdesc.tau[g][0], 4 * cells,
                                             cudaMemcpyDeviceToDevice, s->stream));
     }
@@ -776,7 +818,8 @@ int sim_load(sim_t *s, const void *buf, size_t len)
 int sim_set_variant(sim_t *s, int variant)
 {
     if (!s || (variant != kVariantPipeline && variant != kVariantTwoPass &&
-               variant != kVariantFused && variant != kVariantAgent))
+               variant != kVariantFused && variant != kVariantAgent &&
+               variant != kVariantDeferred))
         return fail(s, PEDSIM_EINVAL, "unknown variant");
     if (variant == s->variant) return PEDSIM_OK;
     // each variant starts from its own default tile shape
@@ -785,7 +828,7 @@ int sim_set_variant(sim_t *s, int variant)
 
 int sim_set_tiling(sim_t *s, int tile_w, int tile_h, int ctas_per_sm)
 {
-    const bool ok = s && s->variant != kVariantAgent && s->variant != kVariantTwoPass &&
+    const bool ok = s && !self_advancing(s->variant) && s->variant != kVariantTwoPass &&
                     (s->variant == kVariantFused ? tile_supported(tile_w, tile_h)
                                                  : pipeline_tile_supported(tile_w, tile_h));
     if (!ok || ctas_per_sm < 0 || ctas_per_sm > 32)
@@ -799,13 +842,23 @@ int sim_set_tiling(sim_t *s, int tile_w, int tile_h, int ctas_per_sm)
 int sim_launches_per_step(sim_t *s, int *out)
 {
     if (!s || !out) return fail(s, PEDSIM_EINVAL, "null argument");
-    if (s->variant == kVariantAgent)
-        *out = 2;  // proposals and stream, then the resolution (it advances the step)
+    if (self_advancing(s->variant))
+        *out = 2;  // proposals (and stream), then the resolution (it advances the step)
     else if (s->variant == kVariantFused)
         *out = 2;  // the step and the step-index advance
     else
         *out = 3;  // proposals, resolution and the step-index advance
     return PEDSIM_OK;
+}
+
+int sim_set_wait_test(sim_t *s, uint64_t wait_cycles, uint32_t test_flags)
+{
+    if (!s) return PEDSIM_EINVAL;
+    if (test_flags & ~(uint32_t)PEDSIM_TEST_SKIP_RESOLVE_LOADS)
+        return fail(s, PEDSIM_EINVAL, "unknown test flag");
+    s->wait_cycles = (unsigned long long)wait_cycles;
+    s->test_flags = test_flags;
+    return upload_desc(s);
 }
 
 int sim_device_status(sim_t *s)
@@ -847,8 +900,8 @@ namespace {
 // the (scenario, tile) work list, and the graph of kGraphSteps steps.
 struct MultiRun {
     ScenarioDesc *d_descs = nullptr;
-    uint32_t *d_prefix = nullptr;  // tile, cell-block and agent-block prefixes (3 x capacity + 1)
-    uint32_t cell_total = 0, agent_total = 0;
+    uint32_t *d_prefix = nullptr;  // tile, cell-block, agent-block, slice prefixes (4 x capacity + 1)
+    uint32_t cell_total = 0, agent_total = 0, slice_total = 0;
     ActivityCtl *d_act = nullptr;  // tile activity of the shared fused launches
     size_t act_capacity = 0;       // bytes
     int capacity = 0, count = 0, prefix_n = 0;
@@ -878,7 +931,7 @@ struct MultiRun {
                                         sizeof(ScenarioDesc) * (size_t)cap_new, stream);
         if (e == cudaSuccess)
             e = cudaMallocAsync(reinterpret_cast<void **>(&d_prefix),
-                                3 * sizeof(uint32_t) * (size_t)(cap_new + 1), stream);
+                                4 * sizeof(uint32_t) * (size_t)(cap_new + 1), stream);
         if (e != cudaSuccess) return cuda_(e, "work list allocation");
         capacity = cap_new;
         return PEDSIM_OK;
@@ -891,17 +944,21 @@ struct MultiRun {
         if (rc) return rc;
         const size_t n = sims.size();
         std::vector<ScenarioDesc> h(n);
-        std::vector<uint32_t> pre(3 * (n + 1), 0);  // tiles, cell blocks, agent blocks
+        // tiles, cell blocks, agent blocks, refresh slices of the deferred step
+        std::vector<uint32_t> pre(4 * (n + 1), 0);
         for (size_t i = 0; i < n; ++i) {
             h[i] = sims[i]->hdesc;
+            const uint32_t cb = cell_blocks(sims[i]->W, sims[i]->H, sims[i]->p);
             pre[i + 1] = pre[i] + (uint32_t)(h[i].tiles_x * h[i].tiles_y);
-            pre[n + 1 + i + 1] = pre[n + 1 + i] + cell_blocks(sims[i]->W, sims[i]->H, sims[i]->p);
+            pre[n + 1 + i + 1] = pre[n + 1 + i] + cb;
             pre[2 * (n + 1) + i + 1] = pre[2 * (n + 1) + i] + agent_blocks(sims[i]->p.n_per_side);
+            pre[3 * (n + 1) + i + 1] = pre[3 * (n + 1) + i] + deferred_slices(cb);
         }
         count = (int)n;
         total = pre[n];
         cell_total = pre[2 * n + 1];
         agent_total = pre[3 * n + 2];
+        slice_total = pre[4 * n + 3];
         const size_t need = activity_bytes(std::max(total, 1u));
         if (need > act_capacity) {
             if (d_act) cudaFreeAsync(d_act, stream);
@@ -950,10 +1007,14 @@ struct MultiRun {
                 : variant == kVariantAgent
                     ? launch_agent_step(d_descs, d_prefix + (n + 1), d_prefix + 2 * (n + 1), count,
                                         cell_total, agent_total, d_act, st)
+                : variant == kVariantDeferred
+                    ? launch_deferred_step(d_descs, d_prefix + (n + 1), d_prefix + 2 * (n + 1),
+                                           d_prefix + 3 * (n + 1), count, slice_total,
+                                           agent_total, d_act, st)
                     : launch_pipeline_step(d_descs, d_prefix, count, total, i, tile_h, st);
             if (e != cudaSuccess) return cuda_(e, "batched step launch");
         }
-        if (variant == kVariantAgent) return PEDSIM_OK;  // the step advanced itself
+        if (self_advancing(variant)) return PEDSIM_OK;  // the step advanced itself
         cudaError_t e = launch_advance(d_descs, count, k, st);
         if (e != cudaSuccess) return cuda_(e, "advance launch");
         return PEDSIM_OK;
@@ -1091,7 +1152,7 @@ int sim_batch_read_grid(batch_t *b, int i, uint8_t *occ, uint32_t *ids, float *t
 int sim_batch_set_tiling(batch_t *b, int tile_w, int tile_h, int ctas_per_sm)
 {
     if (!b) return PEDSIM_EINVAL;
-    const bool ok = b->run.variant != kVariantAgent &&
+    const bool ok = !self_advancing(b->run.variant) &&
                     (b->run.variant == kVariantFused ? tile_supported(tile_w, tile_h)
                                                      : pipeline_tile_supported(tile_w, tile_h));
     if (!ok || ctas_per_sm < 0 || ctas_per_sm > 32) return PEDSIM_EINVAL;
@@ -1108,7 +1169,7 @@ int sim_batch_set_tiling(batch_t *b, int tile_w, int tile_h, int ctas_per_sm)
 int sim_batch_set_variant(batch_t *b, int variant)
 {
     if (!b || (variant != kVariantPipeline && variant != kVariantFused &&
-               variant != kVariantAgent))
+               variant != kVariantAgent && variant != kVariantDeferred))
         return PEDSIM_EINVAL;
     b->run.variant = variant;
     const int tw = variant == kVariantFused ? 64 : 128;

@@ -39,11 +39,23 @@ namespace pedsim {
 //   acode         uint8 per agent: proposal code | group << 4 of the current
 //                 step, | 0x80 once the agent has moved (agent-parallel
 //                 variant)
-//   claim[q]      uint8 claim-mask planes of the agent-parallel variant: at
-//                 step t, claim[t & 1] holds at each target cell bit j for
-//                 its claimant at scan offset j; the other plane is cleared
-//                 at the previous step's targets during the same step
+//   codes[q]      uint8 code planes of the agent-parallel variant: at step
+//                 t, codes[t & 1] holds each agent's direction code (0 =
+//                 stay) at its cell and 0 at every cell empty at t; the
+//                 resolution gathers a target's claimants from its eight
+//                 neighbours there
+//   wait_cycles   SM clock cycles after which a bounded wait of the tiled
+//                 variant gives up (0 = kWaitCycles, about 2 s)
+//   stamp         uint8 per cell (ACO), deferred-evaporation variant: the low
+//                 byte of the step at which the cell's values in tau[g][0]
+//                 are valid (the variant keeps one plane per group, updated
+//                 in place)
+//   test_flags    failure-detection test hook: with kTestSkipResolveLoads the
+//                 tiled resolution kernel issues none of its TMA loads, so
+//                 its bounded wait runs out and it returns without writing
+//                 any state
 constexpr int kDescHeaderBytes = 256;
+constexpr uint32_t kTestSkipResolveLoads = 1u;
 
 struct alignas(128) ScenarioDesc {
     unsigned long long step;
@@ -70,8 +82,12 @@ struct alignas(128) ScenarioDesc {
     int *error;
     uint32_t *pos;
     uint8_t *acode;
-    uint8_t *claim[2];
-    uint8_t header_pad_[kDescHeaderBytes - 96 - 16 * 8];
+    uint8_t *codes[2];
+    unsigned long long wait_cycles;  // limit of the tiled variant's bounded waits (0 = default)
+    uint32_t test_flags;             // kTestSkipResolveLoads (failure-detection test only)
+    uint32_t pad1_;
+    uint8_t *stamp;                  // deferred-evaporation stamps (ACO)
+    uint8_t header_pad_[kDescHeaderBytes - 96 - 16 * 8 - 24];
     // TMA tensor maps; boxes follow the variant and tile shape:
     //   tiled two-kernel step: occ (tile_w + 32) x (tile_h + 2), occ_out and
     //   prop_out tile_w x tile_h, prop (tile_w + 32) x (tile_h + 4), tau
@@ -116,7 +132,8 @@ enum { kMoved = 0, kConflicts = 1, kCrossedA = 2, kCrossedB = 3, kNumCounters = 
 enum { kGridCounts = 4 };
 
 // Step-kernel variants.
-enum { kVariantPipeline = 0, kVariantTwoPass = 1, kVariantFused = 2, kVariantAgent = 3 };
+enum { kVariantPipeline = 0, kVariantTwoPass = 1, kVariantFused = 2, kVariantAgent = 3,
+       kVariantDeferred = 4 };
 
 // Work units of the agent-parallel variant: cells per CTA of its streaming
 // pass (8 per thread: measured best among 4, 8, 16 and 32 at 2048^2 and
@@ -162,8 +179,18 @@ cudaError_t launch_two_pass_step(const ScenarioDesc *d_desc, uint8_t *d_prop, in
 cudaError_t launch_agent_step(const ScenarioDesc *d_descs, const uint32_t *d_cell_prefix,
                               const uint32_t *d_agent_prefix, int n, uint32_t cell_blocks,
                               uint32_t agent_blocks, ActivityCtl *ctl, cudaStream_t stream);
+// Deferred-evaporation step over scenarios [0, n) (the agent-parallel step
+// without the dense stream; see pedsim_agent.cu): slice_prefix[i] = first
+// refresh CTA of scenario i (deferred_slices(its cell blocks) each).
+cudaError_t launch_deferred_step(const ScenarioDesc *d_descs, const uint32_t *d_cell_prefix,
+                                 const uint32_t *d_agent_prefix, const uint32_t *d_slice_prefix,
+                                 int n, uint32_t slices, uint32_t agent_blocks, ActivityCtl *ctl,
+                                 cudaStream_t stream);
+uint32_t deferred_slices(uint32_t cell_blocks);
+// Brings one scenario's deferred pheromone planes up to its current step.
+cudaError_t launch_deferred_catch_up(const ScenarioDesc *d_desc, int cells, cudaStream_t stream);
 // Rebuilds pos[] of one scenario from its occupancy plane `plane` and clears
-// its claim planes and per-agent codes (agent-parallel variant).
+// its code planes and per-agent codes (agent-parallel variant).
 cudaError_t launch_build_pos(const ScenarioDesc *d_desc, int cells, int plane,
                              cudaStream_t stream);
 // step += k (clamped at end_step) for scenarios [0, n).

@@ -91,6 +91,7 @@ __global__ void init_kernel(const ScenarioDesc *__restrict__ descs)
         if (d.model == 1) {
             d.tau[0][0][c] = d.tau0;
             d.tau[1][0][c] = d.tau0;
+            d.stamp[c] = (uint8_t)d.step;  // plane 0 is valid at the step index
         }
     }
     const size_t agents = 2 * (size_t)d.n_per_side + 1;
@@ -1013,10 +1014,11 @@ __device__ __forceinline__ uint32_t nonzero_bytes(uint32_t v)
 // One thread waits (bounded) for the TMA copies behind `bar`; the rest of the
 // CTA blocks in the barrier instead of polling.  Returns false for every
 // thread when the wait gave up.
-__device__ __forceinline__ bool cta_wait_tma(uint64_t *bar, uint32_t parity)
+__device__ __forceinline__ bool cta_wait_tma(uint64_t *bar, uint32_t parity,
+                                             unsigned long long limit)
 {
     bool ok = true;
-    if (threadIdx.x == 0) ok = mbar_wait_bounded(bar, parity);
+    if (threadIdx.x == 0) ok = mbar_wait_bounded(bar, parity, limit ? (long long)limit : kWaitCycles);
     return __syncthreads_and(ok);
 }
 
@@ -1070,7 +1072,7 @@ propose_tile_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__re
         tma_load_2d(occ_s, &gd->map_occ[p], x0 - 16, y0 - 1, &bar);
     }
     __syncthreads();
-    if (!cta_wait_tma(&bar, 0)) {
+    if (!cta_wait_tma(&bar, 0, d.wait_cycles)) {
         if (threadIdx.x == 0) atomicExch(d.error, kErrTimeout);
         return;
     }
@@ -1176,26 +1178,31 @@ resolve_tile_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__re
         const int p = (int)(t & 1);
         const bool aco = d.model == 1;
         if (threadIdx.x == 0) {
-            // The occupancy and pheromone at t come from the resolution of the
-            // step before, complete before this step's proposal kernel
-            // started: they are copied while the proposal kernel still runs.
             mbar_init(&bar, 1);
             fence_mbarrier_init();
-            mbar_arrive_expect_tx(&bar, (TH + 4) * RB + (TH + 2) * RB + (aco ? 2 * TH * TW * 4 : 0));
-            tma_load_2d(occ_s, &gd->map_occ[p], x0 - 16, y0 - 1, &bar);
-            if (aco) {
-                tma_load_2d(tau_s[0], &gd->map_tau[0][p], x0, y0, &bar);
-                tma_load_2d(tau_s[1], &gd->map_tau[1][p], x0, y0, &bar);
+            if (!(d.test_flags & kTestSkipResolveLoads)) {
+                // The occupancy and pheromone at t come from the resolution of
+                // the step before, complete before this step's proposal kernel
+                // started: they are copied while the proposal kernel still runs.
+                mbar_arrive_expect_tx(&bar, (TH + 4) * RB + (TH + 2) * RB +
+                                                (aco ? 2 * TH * TW * 4 : 0));
+                tma_load_2d(occ_s, &gd->map_occ[p], x0 - 16, y0 - 1, &bar);
+                if (aco) {
+                    tma_load_2d(tau_s[0], &gd->map_tau[0][p], x0, y0, &bar);
+                    tma_load_2d(tau_s[1], &gd->map_tau[1][p], x0, y0, &bar);
+                }
+                // the proposals are the proposal kernel's output
+                pdl_wait();
+                tma_load_2d(prop_s, &gd->map_prop, x0 - 16, y0 - 2, &bar);
             }
-            // the proposals are the proposal kernel's output
-            pdl_wait();
-            tma_load_2d(prop_s, &gd->map_prop, x0 - 16, y0 - 2, &bar);
+            // (test hook: no load issued and no arrival, so the wait below
+            // runs out and nothing is in flight when the CTA returns)
         }
         pdl_wait();
         pdl_trigger();
         const int W = d.W, H = d.H;
         __syncthreads();  // barrier initialised
-        if (!cta_wait_tma(&bar, 0)) {
+        if (!cta_wait_tma(&bar, 0, d.wait_cycles)) {
             if (threadIdx.x == 0) atomicExch(d.error, kErrTimeout);
         } else {
             // Claim pass: every proposal of the tile and its 2-ring that targets

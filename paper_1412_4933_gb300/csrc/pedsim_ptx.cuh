@@ -45,12 +45,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return done != 0;
 }
 
-// Waits for the phase with the given parity; false after kWaitCycles.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+// Waits for the phase with the given parity; false after `limit` SM clock
+// cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  long long limit = kWaitCycles)
 {
     const long long start = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - start > kWaitCycles) return false;
+        if (clock64() - start > limit) return false;
     }
     return true;
 }

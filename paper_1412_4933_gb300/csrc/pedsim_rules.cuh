@@ -106,15 +106,24 @@ __device__ __forceinline__ float int_pow(float v, uint32_t e)
     return p;
 }
 
+// Own-group pheromone at offset (dx, dy) from an agent, read from a plane or
+// a shared-memory tile: c points at the agent's own cell, stride is the row
+// pitch in elements.
+struct PlaneTau {
+    const float *c;
+    int stride;
+    __device__ __forceinline__ float operator()(int dx, int dy) const { return c[dy * stride + dx]; }
+};
+
 // Choice of an agent whose forward cell is blocked (Sec. II.A, II.B, IV.c).
 // avail: bit i set when frame neighbour i is in the grid and empty.  For ACO
-// the own-group pheromone at offset (dx, dy) from the agent is
-// tau_c[dy * tau_stride + dx] (tau_c points at the agent's own cell of a
-// plane or of a shared-memory tile).  Kept out of line: it is the rare,
-// heavy path (one Philox block).
-static __device__ __noinline__ int choose_blocked(unsigned avail, int side, const float *tau_c,
-                                                  int tau_stride, uint64_t cell, uint64_t step,
-                                                  uint64_t seed, RuleParams rp)
+// tau(dx, dy) returns the own-group pheromone at step t at offset (dx, dy)
+// from the agent (read only at available neighbours).  Kept out of line: it
+// is the rare, heavy path (one Philox block).
+template <class TauFn>
+static __device__ __noinline__ int choose_blocked(unsigned avail, int side, TauFn tau,
+                                                  uint64_t cell, uint64_t step, uint64_t seed,
+                                                  RuleParams rp)
 {
     const Rand4 r = draw(seed, cell, step, kStreamPropose);
 
@@ -126,7 +135,7 @@ static __device__ __noinline__ int choose_blocked(unsigned avail, int side, cons
             w[i] = 0.0f;
             if (avail & (1u << i)) {
                 const int code = kFrameCode[side][i];
-                const float tv = tau_c[kCodeDY[code] * tau_stride + kCodeDX[code]];
+                const float tv = tau(kCodeDX[code], kCodeDY[code]);
                 w[i] = __fmul_rn(int_pow(tv, rp.alpha), int_pow(kEta[i], rp.beta));
             }
             S = __fadd_rn(S, w[i]);
@@ -173,12 +182,12 @@ static __device__ __noinline__ int choose_blocked(unsigned avail, int side, cons
 
 // Proposal of an agent of group g (1 or 2) at (x, y) in a W x H grid at
 // step t.  `occ(dx, dy)` returns the occupancy byte of the in-grid cell at
-// that offset; tau_c / tau_stride locate the agent's own-group pheromone at
-// t (ACO, see choose_blocked).  Returns the absolute direction code 0..8.
-template <class OccFn>
-__device__ __forceinline__ int propose(int x, int y, int g, int W, int H, uint64_t cell,
-                                       uint64_t step, uint64_t seed, const RuleParams &rp,
-                                       OccFn occ, const float *tau_c, int tau_stride)
+// that offset; `tau` reads the agent's own-group pheromone at t (ACO, see
+// choose_blocked).  Returns the absolute direction code 0..8.
+template <class OccFn, class TauFn>
+__device__ __forceinline__ int propose_with(int x, int y, int g, int W, int H, uint64_t cell,
+                                            uint64_t step, uint64_t seed, const RuleParams &rp,
+                                            OccFn occ, TauFn tau)
 {
     const int side = g - 1;
     // an agent on its goal edge column stays (Sec. III)
@@ -195,7 +204,17 @@ __device__ __forceinline__ int propose(int x, int y, int g, int W, int H, uint64
     }
     // forward first (Sec. III): no further calculation when #1 is free
     if (avail & 2u) return kFrameCode[side][1];
-    return choose_blocked(avail, side, tau_c, tau_stride, cell, step, seed, rp);
+    return choose_blocked(avail, side, tau, cell, step, seed, rp);
+}
+
+// The same with the pheromone read from a plane or tile (tau_c points at the
+// agent's own cell, tau_stride is the row pitch).
+template <class OccFn>
+__device__ __forceinline__ int propose(int x, int y, int g, int W, int H, uint64_t cell,
+                                       uint64_t step, uint64_t seed, const RuleParams &rp,
+                                       OccFn occ, const float *tau_c, int tau_stride)
+{
+    return propose_with(x, y, g, W, H, cell, step, seed, rp, occ, PlaneTau{tau_c, tau_stride});
 }
 
 // Scan index of the winning claimant of a cell with claim mask m (bit j set:

@@ -25,7 +25,8 @@ _lib = C.CDLL(LIB_PATH)
 
 OK, EINVAL, ENOMEM, ENOSPC, ECUDA, ETIMEDOUT, ENOENT = 0, -22, -12, -28, -5, -110, -2
 LEM, ACO = 0, 1
-VARIANT_TILED, VARIANT_TWO_PASS, VARIANT_FUSED, VARIANT_AGENT = 0, 1, 2, 3
+VARIANT_TILED, VARIANT_TWO_PASS, VARIANT_FUSED, VARIANT_AGENT, VARIANT_DEFERRED = 0, 1, 2, 3, 4
+TEST_SKIP_RESOLVE_LOADS = 1
 
 
 class SimParams(C.Structure):
@@ -63,6 +64,7 @@ _SIGS = {
     "sim_set_variant": (C.c_int, [_P, C.c_int]),
     "sim_set_tiling": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
     "sim_device_status": (C.c_int, [_P]),
+    "sim_set_wait_test": (C.c_int, [_P, C.c_uint64, C.c_uint32]),
     "sim_launches_per_step": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "sim_destroy": (None, [_P]),
     "sim_last_error": (C.c_char_p, [_P]),
@@ -221,6 +223,10 @@ class Sim:
 
     def device_status(self) -> int:
         return int(_lib.sim_device_status(self._h))
+
+    def set_wait_test(self, wait_cycles: int = 0, flags: int = 0) -> None:
+        """Failure-detection test hook (``sim_set_wait_test``)."""
+        self._check(_lib.sim_set_wait_test(self._h, wait_cycles, flags))
 
     def launches_per_step(self) -> int:
         """Kernel launches of one step(1) call with the current variant."""

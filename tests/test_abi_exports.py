@@ -62,15 +62,15 @@ def test_host_only_entry_points(lib_path):
         assert P.validate(W, H, prm) == P.EINVAL
         assert P.device_bytes(W, H, prm) == 0
     # ACO 2048^2 with 100K agents: 2 occupancy planes, the proposal plane,
-    # 2 claim planes, ids, 4 pheromone planes (25 bytes per cell) plus
-    # per-agent arrays (arrival, position, code: 0.9 MB), counter slots and
-    # the tile-activity block
+    # 2 code planes, ids, 4 pheromone planes, the deferred-evaporation stamps
+    # (26 bytes per cell) plus per-agent arrays (arrival, position, code:
+    # 0.9 MB), counter slots and the tile-activity block
     from paper_1412_4933_gb300 import workloads as WL
     prm = P.params_of(WL.ACO_2048)
     nbytes = P.device_bytes(2048, 2048, prm)
     cells = 2048 * 2048
-    assert 25 * cells <= nbytes < 25 * cells + 2 * 2**20
-    # LEM keeps no pheromone planes: 2 occupancy, proposal, 2 claim planes and
+    assert 26 * cells <= nbytes < 26 * cells + 2 * 2**20
+    # LEM keeps no pheromone planes: 2 occupancy, proposal, 2 code planes and
     # ids (9 bytes per cell) plus small arrays
     lem = P.params_of(WL.LEM_256)
     assert 9 * 256 * 256 <= P.device_bytes(256, 256, lem) < 10 * 256 * 256

@@ -21,8 +21,8 @@ from paper_1412_4933_gb300 import pedsim as P  # noqa: E402
 
 # Step variants that keep their own state between steps (the two-pass
 # variant is the plain baseline and runs on the small grids only).
-VARIANTS = [P.VARIANT_TILED, P.VARIANT_FUSED, P.VARIANT_AGENT]
-VARIANT_IDS = ["tiled", "fused", "agent"]
+VARIANTS = [P.VARIANT_TILED, P.VARIANT_FUSED, P.VARIANT_AGENT, P.VARIANT_DEFERRED]
+VARIANT_IDS = ["tiled", "fused", "agent", "deferred"]
 
 
 def oparams(sc):
@@ -247,7 +247,7 @@ def test_launches_per_step_query():
     sim = P.Sim(sc.W, sc.H, P.params_of(sc))
     try:
         for v, n in ((P.VARIANT_AGENT, 2), (P.VARIANT_FUSED, 2), (P.VARIANT_TILED, 3),
-                     (P.VARIANT_TWO_PASS, 3)):
+                     (P.VARIANT_TWO_PASS, 3), (P.VARIANT_DEFERRED, 2)):
             sim.set_variant(v)
             assert sim.launches_per_step() == n
     finally:
@@ -326,9 +326,60 @@ def test_variant_switch_mid_run():
     agent variant rebuilds its positions from the planes)."""
     sc = SMALL[2]
     sim, orc = make_pair(sc, P.VARIANT_TILED)
-    for v in (P.VARIANT_AGENT, P.VARIANT_FUSED, P.VARIANT_AGENT, P.VARIANT_TILED):
+    for v in (P.VARIANT_AGENT, P.VARIANT_FUSED, P.VARIANT_AGENT, P.VARIANT_DEFERRED,
+              P.VARIANT_TILED, P.VARIANT_DEFERRED, P.VARIANT_AGENT, P.VARIANT_DEFERRED,
+              P.VARIANT_FUSED):
         sim.set_variant(v)
         sim.step(13)
         orc.step(13)
         assert_same(sim, orc, f"after variant {v}")
     assert sim.stats() == orc.stats()
+
+
+# --------------------------------------------------------------------------
+# Deferred evaporation: values are brought up to date only where read and in
+# a rolling refresh, so they must be compared after runs with no read-back
+# in between (every read-back brings every cell up to date first).
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("sc", SMALL[1:3] + [EDGE[0], EDGE[4], EDGE[6], EDGE[8]],
+                         ids=lambda s: s.name)
+def test_deferred_sparse_read_back(sc):
+    sim, orc = make_pair(sc, P.VARIANT_DEFERRED)
+    done = 0
+    # gaps shorter and longer than the 32-step refresh period, odd and even
+    # end steps, plain launches and graph replays
+    for gap in (1, 5, 31, 32, 33, 16, 47, 64, 3):
+        sim.step(gap)
+        orc.step(gap)
+        done += gap
+        assert_same(sim, orc, f"{sc.name} step {done}")
+        assert sim.stats() == orc.stats()
+    assert sim.device_status() == 0
+
+
+def test_deferred_aco_2048_full_run():
+    """The 100K-agent ACO workload for its full 2000 steps with deferred
+    evaporation, compared at a few steps only (values age between them)."""
+    sc = WL.ACO_2048
+    sim, orc = make_pair(sc, P.VARIANT_DEFERRED)
+    done = 0
+    for target in (7, 40, 333, 1000, 2000):
+        sim.step(target - done)
+        orc.step(target - done)
+        done = target
+        assert_same(sim, orc, f"{sc.name} deferred step {target}")
+        assert sim.stats() == orc.stats()
+    assert sim.device_status() == 0
+    sim.close()
+
+
+def test_deferred_rejects_tiling_and_reports_two_launches():
+    sc = SMALL[1]
+    sim = P.Sim(sc.W, sc.H, P.params_of(sc))
+    try:
+        sim.set_variant(P.VARIANT_DEFERRED)
+        assert sim.launches_per_step() == 2
+        with pytest.raises(P.PedsimError):
+            sim.set_tiling(64, 16, 0)
+    finally:
+        sim.close()
