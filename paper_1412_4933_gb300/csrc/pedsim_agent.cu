@@ -43,6 +43,7 @@
 namespace pedsim {
 
 constexpr int kMaxDevices = 64;  // devices whose occupancy is cached
+constexpr uint8_t kClaimed = 0x80;  // code-plane byte of an empty cell some agent proposed
 
 
 // Scenario of work block b (prefix[i] = first block of scenario i).
@@ -57,39 +58,180 @@ __device__ __forceinline__ int block_scenario(const uint32_t *__restrict__ prefi
     return lo;
 }
 
-// Proposal of agent index a (id a + 1) at step t.  The agent's direction
-// code goes to its per-agent byte and to its own cell of code plane t & 1
-// (written every step, 0 for "stay"), where the resolution gathers it.  An
-// agent that moved during the previous step also clears its old cell in both
-// code planes: the plane of t - 1 holds its code of t - 1 there and the plane
-// of t may still hold its code of t - 2, and nobody else writes that cell
-// before step t + 1 (it was vacated at t - 1, so it is empty at t).  So at
-// every step the planes hold a nonzero code only at cells occupied at that
-// step.
-__device__ __forceinline__ void propose_agent(const ScenarioDesc &d, uint32_t a, uint64_t t)
-{
-    const uint32_t id = a + 1u;
-    const int W = d.W, H = d.H;
-    const uint32_t cell = __ldg(d.pos + id);
-    const int prev = __ldg(d.acode + id);
-    const int x = (int)(cell % (uint32_t)W), y = (int)(cell / (uint32_t)W);
-    const int p = (int)(t & 1);
-    const uint8_t *occ = d.occ[0];
-    const int g = __ldg(occ + cell);
-    const float *tp = d.tau[g == 2 ? 1 : 0][p];
-    const RuleParams rp{d.model, d.alpha, d.beta, d.lem_scale};
-    const int code = propose(
-        x, y, g, W, H, (uint64_t)cell, t, d.seed, rp,
-        [&](int dx, int dy) { return (int)__ldg(occ + ((int64_t)cell + (int64_t)dy * W + dx)); },
-        tp ? tp + cell : nullptr, W);
-    if (prev & 0x80) {
-        const int pc = prev & 15;
-        const int64_t old_cell = (int64_t)cell - ((int64_t)kCodeDY[pc] * W + kCodeDX[pc]);
-        d.codes[0][old_cell] = 0;
-        d.codes[1][old_cell] = 0;
+// Own-group pheromone of a blocked agent's neighbours, loaded together with
+// its occupancy before it was known whether the forward cell is free (the
+// blocked agents then skip a dependent round of loads): v[i] and, for the
+// deferred step, stamp[i] of frame neighbour i (zero outside the grid).
+// finish() brings deferred values up to step `now`, the neighbours'
+// evaporation chains interleaved.
+struct PrefetchedTau {
+    const float *v;
+    const uint8_t *stamp;  // nullptr: the values are current
+    uint32_t now;
+    float q;
+    __device__ __forceinline__ float fetch(int i, int, uint32_t &aux) const
+    {
+        aux = stamp ? stamp[i] : 0u;
+        return v[i];
     }
-    d.codes[p][cell] = (uint8_t)code;
-    d.acode[id] = (uint8_t)(code | (g << 4));
+    __device__ __forceinline__ void finish(float (&tv)[9], const uint32_t (&aux)[9],
+                                           unsigned avail) const
+    {
+        if (!stamp) return;
+        uint32_t age[9], most = 0;
+#pragma unroll
+        for (int i = 2; i <= 8; ++i) {
+            age[i] = (avail & (1u << i)) ? (now - aux[i]) & 255u : 0u;
+            most = age[i] > most ? age[i] : most;
+        }
+        for (uint32_t k = 0; k < most; ++k) {
+#pragma unroll
+            for (int i = 2; i <= 8; ++i)
+                if (k < age[i]) tv[i] = __fmul_rn(tv[i], q);
+        }
+    }
+};
+
+// Loads issued where they stand (the compiler may not sink them into the
+// blocked agents' branch, which would cost that branch a round trip).
+__device__ __forceinline__ float ld_nc_f32(const float *p)
+{
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_nc_u8(const uint8_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.global.nc.u8 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// A forward-blocked agent waiting for the full rule (Eq. 1 / Eq. 2): its
+// prefetched pheromone and stamps, cell, id and frame state.
+struct BlockedAgent {
+    float v[9];
+    uint8_t stamp[12];
+    uint32_t cell, id;
+    uint32_t avail, g;
+};
+
+// Proposals of agent block lb (kAgentBlock agents, one per thread; every
+// thread of the CTA calls this) at step t.  The agent's group is known from
+// its per-agent byte (kept there from placement on), so its own-group
+// pheromone around it (with the stamps, for the deferred step) is loaded in
+// the same round as the occupancy.  Forward first (Sec. III) decides most
+// agents at once; the blocked ones are compacted into a shared list (warp
+// ballots and a scan over the CTA's warps) and take the full rule one per
+// thread, so its heavy path (a Philox block, the roulette) runs in as few
+// full warps as there are blocked agents instead of in every warp that has
+// one.
+//
+// Code plane t & 1 after the proposals of step t: at every occupied cell its
+// agent's direction code (0 = stay), kClaimed at every empty cell some agent
+// proposed, 0 elsewhere.  (A cell is never both occupied and proposed at one
+// step, so one byte holds either.)  The resolution gathers a target's
+// claimants from its neighbours' codes; the claimed flags only let the
+// streams skip the cells the winners write.  Every proposer of a cell writes
+// the same flag with a plain store.  Keeping the plane clean: an agent
+// overwrites its own cell every step; a winner clears its old cell in the
+// plane of the next step (in the resolution, where no one reads that plane)
+// and, at the next step's proposals, in the plane of the step it moved in
+// (no one writes that plane then); a claimed cell always receives its
+// winner, whose later overwrite or clear removes the flag.
+template <bool Deferred>
+__device__ __forceinline__ void propose_block(const ScenarioDesc &d, uint32_t lb, uint64_t t);
+
+template <bool Deferred>
+__device__ __forceinline__ void propose_block(const ScenarioDesc &d, uint32_t lb, uint64_t t)
+{
+    __shared__ BlockedAgent blocked[kAgentBlock];
+    __shared__ uint32_t warp_base[kAgentBlock / 32 + 1];
+    const uint32_t a = lb * kAgentBlock + threadIdx.x;
+    const bool live = t < d.end_step && a < 2u * d.n_per_side;
+    const int W = d.W, H = d.H;
+    const int p = (int)(t & 1);
+    bool is_blocked = false;
+    uint32_t id = 0, cell = 0, avail = 0;
+    int g = 1;
+    float pre[9];
+    uint32_t pst[9];
+    if (live) {
+        id = a + 1u;
+        cell = __ldg(d.pos + id);
+        const int prev = __ldg(d.acode + id);
+        g = prev >> 4 & 3;
+        const int x = (int)(cell % (uint32_t)W), y = (int)(cell / (uint32_t)W);
+        const uint8_t *occ = d.occ[0];
+        const float *tp = d.tau[g == 2 ? 1 : 0][Deferred ? 0 : p];
+        const int side = g - 1;
+        if (tp) {
+#pragma unroll
+            for (int i = 1; i <= 8; ++i) {
+                const int code = kFrameCode[side][i];
+                const int nx = x + kCodeDX[code], ny = y + kCodeDY[code];
+                const bool inside = (unsigned)nx < (unsigned)W && (unsigned)ny < (unsigned)H;
+                const int64_t off = (int64_t)cell + (int64_t)kCodeDY[code] * W + kCodeDX[code];
+                pre[i] = inside ? ld_nc_f32(tp + off) : 0.0f;
+                pst[i] = Deferred && inside ? ld_nc_u8(d.stamp + off) : 0u;
+            }
+        }
+        int code = 0;
+        if (!parked(x, g, W)) {
+            avail = frame_avail(x, y, g, W, H, [&](int dx, int dy) {
+                return (int)__ldg(occ + ((int64_t)cell + (int64_t)dy * W + dx));
+            });
+            if (avail & 2u) code = kFrameCode[side][1];
+            else is_blocked = true;
+        }
+        if (prev & 0x80) {
+            const int pc = prev & 15;
+            const int64_t old_cell = (int64_t)cell - ((int64_t)kCodeDY[pc] * W + kCodeDX[pc]);
+            d.codes[p ^ 1][old_cell] = 0;  // its code of t - 1 there
+        }
+        if (!is_blocked) {
+            d.codes[p][cell] = (uint8_t)code;
+            if (code) d.codes[p][(int64_t)cell + (int64_t)kCodeDY[code] * W + kCodeDX[code]] = kClaimed;
+            d.acode[id] = (uint8_t)(code | (g << 4));
+        }
+    }
+    // compaction of the blocked agents
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const unsigned ballot = __ballot_sync(0xffffffffu, is_blocked);
+    if (lane == 0) warp_base[warp + 1] = (uint32_t)__popc(ballot);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        warp_base[0] = 0;
+        for (int w = 1; w <= kAgentBlock / 32; ++w) warp_base[w] += warp_base[w - 1];
+    }
+    __syncthreads();
+    if (is_blocked) {
+        BlockedAgent &e = blocked[warp_base[warp] + __popc(ballot & ((1u << lane) - 1u))];
+        if (d.tau[0][0]) {
+#pragma unroll
+            for (int i = 1; i <= 8; ++i) {
+                e.v[i] = pre[i];
+                if (Deferred) e.stamp[i] = (uint8_t)pst[i];
+            }
+        }
+        e.cell = cell;
+        e.id = id;
+        e.avail = avail;
+        e.g = (uint32_t)g;
+    }
+    __syncthreads();
+    const uint32_t nb = warp_base[kAgentBlock / 32];
+    if (threadIdx.x < nb) {
+        const BlockedAgent &e = blocked[threadIdx.x];
+        const RuleParams rp{d.model, d.alpha, d.beta, d.lem_scale};
+        const int code = choose_blocked(e.avail, (int)e.g - 1,
+                                        PrefetchedTau{e.v, Deferred ? e.stamp : nullptr,
+                                                      (uint32_t)t, d.q},
+                                        (uint64_t)e.cell, t, d.seed, rp);
+        d.codes[p][e.cell] = (uint8_t)code;
+        if (code) d.codes[p][(int64_t)e.cell + (int64_t)kCodeDY[code] * W + kCodeDX[code]] = kClaimed;
+        d.acode[e.id] = (uint8_t)(code | (e.g << 4));
+    }
 }
 
 // Evaporation of cell block b (kCellBlock cells) of the work list's
@@ -187,66 +329,8 @@ agent_stage1_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__re
     } else {
         const int s = block_scenario(agent_prefix, n_scen, b);
         const ScenarioDesc &d = descs[s];
-        const uint64_t t = d.step;
-        const uint32_t a = (b - __ldg(agent_prefix + s)) * kAgentBlock + threadIdx.x;
-        if (t < d.end_step && a < 2u * d.n_per_side) propose_agent(d, a, t);
+        propose_block<false>(d, b - __ldg(agent_prefix + s), d.step);
     }
-}
-
-// The codes a cell block's claim test reads, staged in shared memory: for
-// dy = -1, 0, 1, row dy + 1 holds the code plane's bytes c0 + dy * W - 1 ..
-// c0 + dy * W + kCellBlock (0 outside the plane), so cell c0 + k finds its
-// neighbour (dx, dy) at rows[dy + 1][k + 1 + dx].  Loaded with 8-byte
-// accesses by the whole CTA (cell blocks start at multiples of kCellBlock,
-// W is a multiple of 16, so every window start is 8-byte aligned after the
-// one-byte shift handled here).
-constexpr int kClaimRow = kCellBlock + 16;  // staged bytes per row (>= kCellBlock + 2)
-
-__device__ __forceinline__ void stage_claim_rows(uint8_t (*rows)[kClaimRow],
-                                                 const uint8_t *__restrict__ codes, size_t cells,
-                                                 int W, size_t c0)
-{
-    // rows[r][i] = codes[base_r - 8 + i], base_r = c0 + dy * W (i in 0 .. kClaimRow)
-    constexpr int kWords = kClaimRow / 8;
-    for (int i = threadIdx.x; i < 3 * kWords; i += kAgentBlock) {
-        const int r = i / kWords, w = i - r * kWords;
-        const int64_t start = (int64_t)c0 + (int64_t)(r - 1) * W - 8 + 8 * w;
-        uint2 v = make_uint2(0u, 0u);
-        if (start >= 0 && start + 8 <= (int64_t)cells)
-            v = __ldcg(reinterpret_cast<const uint2 *>(codes + start));
-        *reinterpret_cast<uint2 *>(&rows[r][8 * w]) = v;
-    }
-}
-
-// Claim flags of the four cells c0 + k .. c0 + k + 3 (k a multiple of 4, x
-// the column of the first): byte i of the result is nonzero when a neighbour
-// of cell c0 + k + i proposed it (gather: the claimant at offset (dx, dy)
-// from the cell holds the code of the move (-dx, -dy)).
-__device__ __forceinline__ uint32_t claimed4_staged(const uint8_t (*rows)[kClaimRow], int k, int x,
-                                                    int W)
-{
-    uint32_t hit = 0;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        // bytes k+7 .. k+14 of the staged row are the cells k-1 .. k+6
-        const uint32_t w0 = *reinterpret_cast<const uint32_t *>(&rows[r][k + 4]);
-        const uint32_t w1 = *reinterpret_cast<const uint32_t *>(&rows[r][k + 8]);
-        const uint32_t w2 = *reinterpret_cast<const uint32_t *>(&rows[r][k + 12]);
-        uint32_t left = __byte_perm(w0, w1, 0x6543);   // cells k-1 .. k+2
-        const uint32_t mid = w1;                       // cells k   .. k+3
-        uint32_t right = __byte_perm(w1, w2, 0x4321);  // cells k+1 .. k+4
-        if (x == 0) left &= 0xFFFFFF00u;               // no left neighbour of column 0
-        if (x + 4 == W) right &= 0x00FFFFFFu;          // nor a right one of column W-1
-        const int dy = r - 1;
-        // codes of the moves into the cell from its left, same and right
-        // column of row dy: (+1, -dy), (0, -dy), (-1, -dy)
-        const uint32_t cl = dy < 0 ? 0x08080808u : dy == 0 ? 0x05050505u : 0x03030303u;
-        const uint32_t cc = dy < 0 ? 0x07070707u : 0x02020202u;
-        const uint32_t cr = dy < 0 ? 0x06060606u : dy == 0 ? 0x04040404u : 0x01010101u;
-        hit |= __vcmpeq4(left, cl) | __vcmpeq4(right, cr);
-        if (dy != 0) hit |= __vcmpeq4(mid, cc);
-    }
-    return hit;
 }
 
 // Evaporation of cell block b in the resolution kernel, where the proposals
@@ -277,16 +361,13 @@ __device__ __forceinline__ void stream_block_claimed(const ScenarioDesc *__restr
     pdl_wait();  // the proposals of the step are in
     pdl_trigger();
     if (!active) return;
-    const int W = d.W;
-    __shared__ __align__(16) uint8_t rows[3][kClaimRow];
-    stage_claim_rows(rows, d.codes[p], cells, W, c0);
-    __syncthreads();
-    uint32_t cw[kStreamVec];
+    uint32_t cw[kStreamVec];  // claimed flags of the thread's cells
 #pragma unroll
     for (int k = 0; k < kStreamVec; ++k) {
         const size_t c = c0 + 4 * ((size_t)k * kAgentBlock + threadIdx.x);
-        const int kk = 4 * (k * kAgentBlock + (int)threadIdx.x);
-        cw[k] = c < cells ? claimed4_staged(rows, kk, (int)(c % (size_t)W), W) : 0u;
+        cw[k] = c < cells
+                    ? __ldcg(reinterpret_cast<const unsigned int *>(d.codes[p] + c)) & 0x80808080u
+                    : 0u;
     }
     const float q = d.q;
     float *const na = d.tau[0][p ^ 1], *const nb = d.tau[1][p ^ 1];
@@ -404,6 +485,7 @@ __device__ __forceinline__ void resolve_apply(const ScenarioDesc &d, uint64_t t,
     const int tx = (int)(r.cell % (uint32_t)W) + dx;
     d.occ[0][r.target] = (uint8_t)g;
     d.occ[0][r.cell] = 0;
+    d.codes[p ^ 1][r.cell] = 0;  // its old cell, in the plane of step t + 1
     d.pos[r.id] = (uint32_t)r.target;
     d.acode[r.id] = (uint8_t)(r.code | (g << 4) | 0x80);
     d.ids[r.target] = r.id;
@@ -560,52 +642,6 @@ __device__ __forceinline__ float evaporate_n(float v, uint32_t age, float q)
     return v;
 }
 
-// Own-group pheromone at step `now` at offset (dx, dy) from an agent: value
-// and stamp at that cell, brought up to date.
-struct DeferredTau {
-    const float *v;
-    const uint8_t *stamp;
-    int stride;
-    uint32_t now;
-    float q;
-    __device__ __forceinline__ float operator()(int dx, int dy) const
-    {
-        const int off = dy * stride + dx;
-        return evaporate_n(__ldg(v + off), (now - (uint32_t)__ldg(stamp + off)) & 255u, q);
-    }
-};
-
-// Proposal of agent index a at step t (as propose_agent; the pheromone of
-// the blocked path is read through the stamps).
-__device__ __forceinline__ void propose_agent_deferred(const ScenarioDesc &d, uint32_t a, uint64_t t)
-{
-    const uint32_t id = a + 1u;
-    const int W = d.W, H = d.H;
-    const uint32_t cell = __ldg(d.pos + id);
-    const int prev = __ldg(d.acode + id);
-    const int x = (int)(cell % (uint32_t)W), y = (int)(cell / (uint32_t)W);
-    const int p = (int)(t & 1);
-    const uint8_t *occ = d.occ[0];
-    const int g = __ldg(occ + cell);
-    const RuleParams rp{d.model, d.alpha, d.beta, d.lem_scale};
-    const float *tp = d.tau[g == 2 ? 1 : 0][0];
-    const auto occ_at = [&](int dx, int dy) {
-        return (int)__ldg(occ + ((int64_t)cell + (int64_t)dy * W + dx));
-    };
-    const int code =
-        tp ? propose_with(x, y, g, W, H, (uint64_t)cell, t, d.seed, rp, occ_at,
-                          DeferredTau{tp + cell, d.stamp + cell, W, (uint32_t)t, d.q})
-           : propose(x, y, g, W, H, (uint64_t)cell, t, d.seed, rp, occ_at, nullptr, W);
-    if (prev & 0x80) {
-        const int pc = prev & 15;
-        const int64_t old_cell = (int64_t)cell - ((int64_t)kCodeDY[pc] * W + kCodeDX[pc]);
-        d.codes[0][old_cell] = 0;
-        d.codes[1][old_cell] = 0;
-    }
-    d.codes[p][cell] = (uint8_t)code;
-    d.acode[id] = (uint8_t)(code | (g << 4));
-}
-
 // First kernel of the deferred step: the proposals only.
 __global__ void __launch_bounds__(kAgentBlock)
 deferred_stage1_kernel(const ScenarioDesc *__restrict__ descs,
@@ -617,9 +653,7 @@ deferred_stage1_kernel(const ScenarioDesc *__restrict__ descs,
     if (b >= agent_blocks) return;
     const int s = block_scenario(agent_prefix, n_scen, b);
     const ScenarioDesc &d = descs[s];
-    const uint64_t t = d.step;
-    const uint32_t a = (b - __ldg(agent_prefix + s)) * kAgentBlock + threadIdx.x;
-    if (t < d.end_step && a < 2u * d.n_per_side) propose_agent_deferred(d, a, t);
+    propose_block<true>(d, b - __ldg(agent_prefix + s), d.step);
 }
 
 // Rolling refresh of cell block b of scenario d at step t: every unclaimed
@@ -644,38 +678,38 @@ __device__ __forceinline__ void refresh_block(const ScenarioDesc &d, uint64_t t,
     }
     pdl_wait();  // the proposals of the step are in
     pdl_trigger();
-    const int W = d.W, p = (int)(t & 1);
+    const int p = (int)(t & 1);
     const uint32_t now = (uint32_t)t, next = (uint32_t)(t + 1) & 255u;
     const float q = d.q;
-    __shared__ __align__(16) uint8_t rows[3][kClaimRow];
-    stage_claim_rows(rows, d.codes[p], cells, W, c0);
-    __syncthreads();
+    // each 4-cell group brought up to step t + 1, the evaporation chains of
+    // its eight values interleaved
 #pragma unroll
     for (int k = 0; k < kStreamVec; ++k) {
         const size_t c = c0 + 4 * ((size_t)k * kAgentBlock + threadIdx.x);
         if (c >= cells) continue;
-        const uint32_t cw =
-            claimed4_staged(rows, 4 * (k * kAgentBlock + (int)threadIdx.x), (int)(c % (size_t)W), W);
-        float a_[4] = {va[k].x, va[k].y, va[k].z, va[k].w};
-        float b_[4] = {vb[k].x, vb[k].y, vb[k].z, vb[k].w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint32_t age = ((now - (sw[k] >> (8 * j))) & 255u) + 1u;
-            a_[j] = evaporate_n(a_[j], age, q);
-            b_[j] = evaporate_n(b_[j], age, q);
+        float a0 = va[k].x, a1 = va[k].y, a2 = va[k].z, a3 = va[k].w;
+        float b0 = vb[k].x, b1 = vb[k].y, b2 = vb[k].z, b3 = vb[k].w;
+        const uint32_t g0 = ((now - sw[k]) & 255u) + 1u, g1 = ((now - (sw[k] >> 8)) & 255u) + 1u;
+        const uint32_t g2 = ((now - (sw[k] >> 16)) & 255u) + 1u, g3 = ((now - (sw[k] >> 24)) & 255u) + 1u;
+        const uint32_t most = max(max(g0, g1), max(g2, g3));
+        for (uint32_t i = 0; i < most; ++i) {
+            if (i < g0) { a0 = __fmul_rn(a0, q); b0 = __fmul_rn(b0, q); }
+            if (i < g1) { a1 = __fmul_rn(a1, q); b1 = __fmul_rn(b1, q); }
+            if (i < g2) { a2 = __fmul_rn(a2, q); b2 = __fmul_rn(b2, q); }
+            if (i < g3) { a3 = __fmul_rn(a3, q); b3 = __fmul_rn(b3, q); }
         }
+        // claimed flags of the four cells
+        const uint32_t cw = __ldcg(reinterpret_cast<const unsigned int *>(d.codes[p] + c)) & 0x80808080u;
         if (cw == 0u) {
-            *reinterpret_cast<float4 *>(d.tau[0][0] + c) = make_float4(a_[0], a_[1], a_[2], a_[3]);
-            *reinterpret_cast<float4 *>(d.tau[1][0] + c) = make_float4(b_[0], b_[1], b_[2], b_[3]);
+            *reinterpret_cast<float4 *>(d.tau[0][0] + c) = make_float4(a0, a1, a2, a3);
+            *reinterpret_cast<float4 *>(d.tau[1][0] + c) = make_float4(b0, b1, b2, b3);
             *reinterpret_cast<unsigned int *>(d.stamp + c) = next * 0x01010101u;
         } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if ((cw >> (8 * j)) & 0xffu) continue;  // the winner writes this cell
-                d.tau[0][0][c + j] = a_[j];
-                d.tau[1][0][c + j] = b_[j];
-                d.stamp[c + j] = (uint8_t)next;
-            }
+            // the winners write the claimed cells
+            if (!(cw & 0xffu)) { d.tau[0][0][c] = a0; d.tau[1][0][c] = b0; d.stamp[c] = (uint8_t)next; }
+            if (!(cw & 0xff00u)) { d.tau[0][0][c + 1] = a1; d.tau[1][0][c + 1] = b1; d.stamp[c + 1] = (uint8_t)next; }
+            if (!(cw & 0xff0000u)) { d.tau[0][0][c + 2] = a2; d.tau[1][0][c + 2] = b2; d.stamp[c + 2] = (uint8_t)next; }
+            if (!(cw & 0xff000000u)) { d.tau[0][0][c + 3] = a3; d.tau[1][0][c + 3] = b3; d.stamp[c + 3] = (uint8_t)next; }
         }
     }
 }
@@ -719,8 +753,32 @@ deferred_resolve_kernel(const ScenarioDesc *__restrict__ descs,
         const uint64_t t = d.step;
         const uint32_t a = lb * kAgentBlock + threadIdx.x;
         bool live = t < d.end_step && a < 2u * d.n_per_side;
+        const bool aco = d.model == 1;
+        const int W = d.W, H = d.H;
         Resolve r;
-        if (live) resolve_load_own(d, a, r);
+        // Before the wait for the proposals: the agent's own entries, then
+        // both groups' values and the stamps of its eight neighbours (the
+        // first kernel writes none of them): whichever neighbour it proposed,
+        // its target's are at hand after the wait.
+        float va[8], vb[8];
+        uint32_t st[8];
+        int x = 0, y = 0;
+        if (live) {
+            resolve_load_own(d, a, r);
+            x = (int)(r.cell % (uint32_t)W);
+            y = (int)(r.cell / (uint32_t)W);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int ox = j < 3 ? j - 1 : j < 5 ? 2 * j - 7 : j - 6;  // scan offset j
+            const int oy = j < 3 ? -1 : j < 5 ? 0 : 1;
+            const bool ok = live && aco && (unsigned)(x + ox) < (unsigned)W &&
+                            (unsigned)(y + oy) < (unsigned)H;
+            const int64_t off = (int64_t)r.cell + (int64_t)oy * W + ox;
+            va[j] = ok ? ld_nc_f32(d.tau[0][0] + off) : 0.0f;
+            vb[j] = ok ? ld_nc_f32(d.tau[1][0] + off) : 0.0f;
+            st[j] = ok ? ld_nc_u8(d.stamp + off) : 0u;
+        }
         pdl_wait();  // proposals complete
         pdl_trigger();
         if (live) {
@@ -731,30 +789,20 @@ deferred_resolve_kernel(const ScenarioDesc *__restrict__ descs,
         if (threadIdx.x == 0) ticket = atomicAdd(&ctl->ticket, 1u);
         Counts cnt;
         if (live) {
-            // the target's neighbours' codes, values and stamp (one round)
-            const int W = d.W, H = d.H;
+            // the target's claimants from its neighbours' codes
             const int dx = kCodeDX[r.code], dy = kCodeDY[r.code];
             r.target = (int64_t)r.cell + (int64_t)dy * W + dx;
-            const int tx = (int)(r.cell % (uint32_t)W) + dx;
-            const bool aco = d.model == 1;
-            float vt = 0.0f, vo = 0.0f;
-            uint32_t age = 0;
-            if (aco) {
-                vt = __ldg(d.tau[r.g == 2 ? 1 : 0][0] + r.target);
-                vo = __ldg(d.tau[r.g == 2 ? 0 : 1][0] + r.target);
-                age = ((uint32_t)t - (uint32_t)__ldg(d.stamp + r.target)) & 255u;
-            }
-            r.mask = gather_claims(d.codes[(int)(t & 1)] + r.target, W, H, tx,
-                                   (int)(r.cell / (uint32_t)W) + dy);
+            const int tx = x + dx;
+            r.mask = gather_claims(d.codes[(int)(t & 1)] + r.target, W, H, tx, y + dy);
             const uint32_t k = (uint32_t)__popc(r.mask);
             const uint32_t mine = 8u - (uint32_t)r.code;
             const uint32_t win =
                 k == 1 ? mine : pick_claimant(r.mask, k, (uint64_t)r.target, t, d.seed);
             if (win == mine) {
                 const int g = r.g;
-                const int tx = (int)(r.cell % (uint32_t)W) + dx;
                 d.occ[0][r.target] = (uint8_t)g;
                 d.occ[0][r.cell] = 0;
+                d.codes[(int)(t & 1) ^ 1][r.cell] = 0;  // its old cell, in the plane of t + 1
                 d.pos[r.id] = (uint32_t)r.target;
                 d.acode[r.id] = (uint8_t)(r.code | (g << 4) | 0x80);
                 d.ids[r.target] = r.id;
@@ -770,12 +818,23 @@ deferred_resolve_kernel(const ScenarioDesc *__restrict__ descs,
                     if (g == 1) ++cnt.crossed_a; else ++cnt.crossed_b;
                 }
                 if (aco) {
+                    // the target is this agent's neighbour at scan offset
+                    // code - 1: its values at t (both groups' chains
+                    // interleaved), then step t's evaporation and the deposit
+                    float ta = 0.0f, tb = 0.0f;
+                    uint32_t ts = 0;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (j == r.code - 1) { ta = va[j]; tb = vb[j]; ts = st[j]; }
                     const float q = d.q;
-                    // values at t, then step t's evaporation and the deposit
-                    vt = __fmul_rn(evaporate_n(vt, age, q), q);
-                    vo = __fmul_rn(evaporate_n(vo, age, q), q);
-                    d.tau[g == 2 ? 1 : 0][0][r.target] = __fadd_rn(vt, dep);
-                    d.tau[g == 2 ? 0 : 1][0][r.target] = vo;
+                    const uint32_t age = (((uint32_t)t - ts) & 255u) + 1u;
+                    for (uint32_t i = 0; i < age; ++i) {
+                        ta = __fmul_rn(ta, q);
+                        tb = __fmul_rn(tb, q);
+                    }
+                    if (g == 1) ta = __fadd_rn(ta, dep); else tb = __fadd_rn(tb, dep);
+                    d.tau[0][0][r.target] = ta;
+                    d.tau[1][0][r.target] = tb;
                     d.stamp[r.target] = (uint8_t)(t + 1);
                 }
                 ++cnt.moved;
@@ -826,11 +885,14 @@ __global__ void build_pos_kernel(const ScenarioDesc *__restrict__ dp, int plane)
     for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells; c += stride) {
         d.codes[0][c] = 0;
         d.codes[1][c] = 0;
-        if (occ[c]) d.pos[d.ids[c]] = (uint32_t)c;
+        if (occ[c]) {
+            // every agent stands on exactly one cell: its position and its
+            // per-agent byte (group, no code yet) are written once
+            const uint32_t id = d.ids[c];
+            d.pos[id] = (uint32_t)c;
+            d.acode[id] = (uint8_t)(occ[c] << 4);
+        }
     }
-    const size_t agents = 2 * (size_t)d.n_per_side + 1;
-    for (size_t a = (size_t)blockIdx.x * blockDim.x + threadIdx.x; a < agents; a += stride)
-        d.acode[a] = 0;
 }
 
 // Resident CTAs of one wave of a kernel on the current device (occupancy

@@ -36,9 +36,10 @@ namespace pedsim {
 //   pos           uint32 cell index of every agent, indexed by id (agent-
 //                 parallel variant; rebuilt from the planes whenever the
 //                 state is set from outside it)
-//   acode         uint8 per agent: proposal code | group << 4 of the current
-//                 step, | 0x80 once the agent has moved (agent-parallel
-//                 variant)
+//   acode         uint8 per agent: proposal code of the current step | group
+//                 << 4 (the group from the moment the positions are built),
+//                 | 0x80 once the agent has moved (agent-parallel and
+//                 deferred variants)
 //   codes[q]      uint8 code planes of the agent-parallel variant: at step
 //                 t, codes[t & 1] holds each agent's direction code (0 =
 //                 stay) at its cell and 0 at every cell empty at t; the

@@ -108,11 +108,21 @@ __device__ __forceinline__ float int_pow(float v, uint32_t e)
 
 // Own-group pheromone at offset (dx, dy) from an agent, read from a plane or
 // a shared-memory tile: c points at the agent's own cell, stride is the row
-// pitch in elements.
+// pitch in elements.  A reader has two phases so that every neighbour's load
+// is issued before any value is used: fetch() loads (value, aux) and
+// finish() turns the fetched entries of the available neighbours into the
+// values at the current step (here they already are).
+// fetch() takes the frame index i (1..8) of the neighbour and its absolute
+// code.
 struct PlaneTau {
     const float *c;
     int stride;
-    __device__ __forceinline__ float operator()(int dx, int dy) const { return c[dy * stride + dx]; }
+    __device__ __forceinline__ float fetch(int, int code, uint32_t &aux) const
+    {
+        aux = 0;
+        return c[kCodeDY[code] * stride + kCodeDX[code]];
+    }
+    __device__ __forceinline__ void finish(float (&)[9], const uint32_t (&)[9], unsigned) const {}
 };
 
 // Choice of an agent whose forward cell is blocked (Sec. II.A, II.B, IV.c).
@@ -128,16 +138,22 @@ static __device__ __noinline__ int choose_blocked(unsigned avail, int side, TauF
     const Rand4 r = draw(seed, cell, step, kStreamPropose);
 
     if (rp.model == 1) {
-        float w[9];
+        float tv[9], w[9];
+        uint32_t aux[9];
+#pragma unroll
+        for (int i = 2; i <= 8; ++i) {
+            tv[i] = 0.0f;
+            aux[i] = 0;
+            if (avail & (1u << i)) {
+                tv[i] = tau.fetch(i, kFrameCode[side][i], aux[i]);
+            }
+        }
+        tau.finish(tv, aux, avail);
         float S = 0.0f;
 #pragma unroll
         for (int i = 2; i <= 8; ++i) {
             w[i] = 0.0f;
-            if (avail & (1u << i)) {
-                const int code = kFrameCode[side][i];
-                const float tv = tau(kCodeDX[code], kCodeDY[code]);
-                w[i] = __fmul_rn(int_pow(tv, rp.alpha), int_pow(kEta[i], rp.beta));
-            }
+            if (avail & (1u << i)) w[i] = __fmul_rn(int_pow(tv[i], rp.alpha), int_pow(kEta[i], rp.beta));
             S = __fadd_rn(S, w[i]);
         }
         if (S > 0.0f) {
@@ -184,16 +200,19 @@ static __device__ __noinline__ int choose_blocked(unsigned avail, int side, TauF
 // step t.  `occ(dx, dy)` returns the occupancy byte of the in-grid cell at
 // that offset; `tau` reads the agent's own-group pheromone at t (ACO, see
 // choose_blocked).  Returns the absolute direction code 0..8.
-template <class OccFn, class TauFn>
-__device__ __forceinline__ int propose_with(int x, int y, int g, int W, int H, uint64_t cell,
-                                            uint64_t step, uint64_t seed, const RuleParams &rp,
-                                            OccFn occ, TauFn tau)
+// An agent on its goal edge column stays there (Sec. III).
+__device__ __forceinline__ bool parked(int x, int g, int W)
+{
+    return (g == 1 && x == W - 1) || (g == 2 && x == 0);
+}
+
+// Bit i (1..8) set when frame neighbour i of an agent of group g at (x, y)
+// is in the grid and empty; occ(dx, dy) reads the in-grid neighbours.
+template <class OccFn>
+__device__ __forceinline__ unsigned frame_avail(int x, int y, int g, int W, int H, OccFn occ)
 {
     const int side = g - 1;
-    // an agent on its goal edge column stays (Sec. III)
-    if ((g == 1 && x == W - 1) || (g == 2 && x == 0)) return 0;
-
-    unsigned avail = 0;  // bit i set: frame neighbour i is in the grid and empty
+    unsigned avail = 0;
 #pragma unroll
     for (int i = 1; i <= 8; ++i) {
         const int code = kFrameCode[side][i];
@@ -202,6 +221,17 @@ __device__ __forceinline__ int propose_with(int x, int y, int g, int W, int H, u
         const bool inside = (unsigned)nx < (unsigned)W && (unsigned)ny < (unsigned)H;
         if (inside && occ(dx, dy) == 0) avail |= 1u << i;
     }
+    return avail;
+}
+
+template <class OccFn, class TauFn>
+__device__ __forceinline__ int propose_with(int x, int y, int g, int W, int H, uint64_t cell,
+                                            uint64_t step, uint64_t seed, const RuleParams &rp,
+                                            OccFn occ, TauFn tau)
+{
+    const int side = g - 1;
+    if (parked(x, g, W)) return 0;
+    const unsigned avail = frame_avail(x, y, g, W, H, occ);
     // forward first (Sec. III): no further calculation when #1 is free
     if (avail & 2u) return kFrameCode[side][1];
     return choose_blocked(avail, side, tau, cell, step, seed, rp);
