@@ -449,41 +449,46 @@ def probe_leg(P, torch, stream, steps=20):
 
 def batched_leg(P, torch, stream, count=256, steps=500):
     """The 256-scenario batch: autotuned launch configuration, then `steps`
-    steps in batched launches, vs one launch per scenario per step."""
+    steps in batched launches, against the same scenarios and steps run one
+    scenario at a time (each scenario's own launches, back to back on the
+    same stream)."""
     from paper_1412_4933_gb300 import autotune
     scs = WL.batched_scenarios(count=count, steps=steps)
     cells = sum(s.cells for s in scs)
+    algo = sum(ALGO_BYTES_PER_CELL[s.model] * s.cells for s in scs)  # bytes per batched step
     choice = autotune.tune(scs, stream=stream)
     batch = P.Batch(scs, stream=stream)
     autotune.apply(batch, choice)
     batch.step(16)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
     batch.step(steps)
+    e1.record(stream)
     torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
+    t_batch = e0.elapsed_time(e1) * 1e-3
     status = batch.device_status()
     batch.close()
-    # one launch per scenario per step, same scenarios (a sample of 32,
-    # scaled by cells)
-    sample = scs[:32]
+    # the same scenarios and steps, one scenario at a time
     sims = []
-    for s in sample:
-        sim = P.Sim(s.W, s.H, P.params_of(s), stream=stream)
-        sim.place(s.seed)
+    for sc in scs:
+        sim = P.Sim(sc.W, sc.H, P.params_of(sc), stream=stream)
+        sim.set_variant(choice[0])
+        if choice[0] not in (P.VARIANT_AGENT, P.VARIANT_DEFERRED):
+            sim.set_tiling(choice[1], choice[2], choice[3])
+        sim.place(sc.seed)
+        sim.step(16)
         sims.append(sim)
+    torch.cuda.synchronize()
+    e0.record(stream)
     for sim in sims:
-        sim.step(1)
+        sim.step(steps)
+    e1.record(stream)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(steps // 10):
-        for sim in sims:
-            sim.step(1)
-    torch.cuda.synchronize()
-    t_single = time.perf_counter() - t0
+    t_single = e0.elapsed_time(e1) * 1e-3
     for sim in sims:
         sim.close()
-    single_rate = sum(s.cells for s in sample) * (steps // 10) / t_single
+    peak, kind = measured_peak()
     cpu = oracle_multicore(scs, steps=50, cores=min(16, os.cpu_count() or 1))
     return {"scenarios": count, "steps": steps, "cells": cells,
             "cpu_oracle_multicore": cpu,
@@ -491,8 +496,48 @@ def batched_leg(P, torch, stream, count=256, steps=500):
                               "ctas_per_sm": choice[3]},
             "scenarios_per_s": count / t_batch,
             "cell_updates_per_s": cells * steps / t_batch,
-            "one_launch_per_scenario_cell_updates_per_s": single_rate,
-            "speedup_vs_one_launch_per_scenario": (cells * steps / t_batch) / single_rate,
+            "algorithmic_bytes_per_step": algo,
+            "algorithmic_bytes_note": "every-step evaporation: 18 B per ACO cell, 2 B per LEM "
+                                      "cell (the deferred variant moves 18/32 B per ACO cell of "
+                                      "dense traffic plus the agents' sparse accesses)",
+            "algorithmic_GBps": algo * steps / t_batch / 1e9,
+            "algorithmic_frac_of_peak": algo * steps / t_batch / 1e9 / peak, "peak_kind": kind,
+            "one_scenario_at_a_time_cell_updates_per_s": cells * steps / t_single,
+            "one_scenario_at_a_time": f"the same {count} scenarios x {steps} steps, each "
+                                      f"scenario's own launches (same variant), back to back",
+            "speedup_vs_one_scenario_at_a_time": t_single / t_batch,
+            "device_status": status}
+
+
+DEFER_PERIOD = 32  # the library's rolling-refresh period of the deferred step
+
+
+def deferred_leg(P, torch, sc, stream, warmup: int, steps: int, repeats: int, headline_s: float):
+    """The <18 B per cell-step scheme: the same step with deferred
+    evaporation (per-cell stamps, values brought up to date where read and
+    in a rolling refresh of 1/32 of the cells per step; bit-identical
+    results), timed exactly like the headline: four instances in turn, one
+    graph of `steps` steps, median of `repeats` replays."""
+    sims = rotating_instances(P, torch, sc, stream, P.VARIANT_DEFERRED, warmup, ROTATING_INSTANCES)
+    g = capture_steps(sims, torch, stream, steps)
+    region = time_graph_repeats(g, torch, stream, repeats)
+    del g
+    status = max(abs(x.device_status()) for x in sims)
+    for x in sims:
+        x.close()
+    step_s = statistics.median(region) / steps
+    dense = 18.0 / DEFER_PERIOD if sc.model == WL.ACO else 0.0
+    return {"variant": "deferred", "steps": steps, "repeats": len(region),
+            "us_per_step": step_s * 1e6,
+            "us_per_step_regions": [r * 1e6 / steps for r in region],
+            "cell_updates_per_s": sc.cells / step_s,
+            "speedup_vs_headline_step": headline_s / step_s,
+            "dense_bytes_per_cell_step": dense,
+            "dense_bytes_per_step": dense * sc.cells,
+            "note": "one pass over every cell every 32 steps (18 B/cell) instead of every step; "
+                    "the agents' accesses (positions, 3x3 occupancy, pheromone and stamps of "
+                    "blocked agents, code planes, winners' writes) come on top and dominate",
+            "gpu_launches_per_step": 2,
             "device_status": status}
 
 
@@ -604,6 +649,9 @@ def run_gpu(args, sc):
     e2e = None
     if rank == 0 and not args.quick:
         e2e = e2e_run(P, torch, sc, stream, reps=2)
+    if rank == 0 and args.variant == "agent":
+        extra["deferred_evaporation"] = deferred_leg(P, torch, sc, stream, args.warmup, args.steps,
+                                                     args.repeats, elapsed_max / args.steps)
     if rank == 0 and not args.quick and not args.no_probe:
         extra["hbm_probe"] = probe_leg(P, torch, stream)
         extra["inputs_larger_than_l2"] = large_inputs_leg(P, torch, sc, stream)

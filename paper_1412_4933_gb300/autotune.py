@@ -1,8 +1,9 @@
 """Autotuner of the batched step's launch configuration.
 
 Knobs: the step variant (tiled two-kernel step with 128 x 8 or 128 x 16
-tiles, the fused persistent kernel with one of its tile shapes, or the
-agent-parallel step, which has no tiles) and, for the persistent kernel, the
+tiles, the fused persistent kernel with one of its tile shapes, the
+agent-parallel step or its deferred-evaporation form, which have no tiles)
+and, for the persistent kernel, the
 CTAs per SM (how many tiles, possibly of different scenarios, an SM works on
 at once).  Each candidate is timed on a scratch
 batch built from the same scenario descriptions (so the tuned batch's own
@@ -20,6 +21,7 @@ import time
 from . import pedsim as P
 
 CANDIDATES = [
+    (P.VARIANT_DEFERRED, 0, 0, 0),
     (P.VARIANT_AGENT, 0, 0, 0),
     (P.VARIANT_TILED, 128, 8, 0),
     (P.VARIANT_TILED, 128, 16, 0),
@@ -69,7 +71,7 @@ def _store_cache(cache: dict) -> None:
 def apply(batch, choice) -> None:
     variant, tw, th, cps = choice
     batch.set_variant(variant)
-    if variant != P.VARIANT_AGENT:
+    if variant not in (P.VARIANT_AGENT, P.VARIANT_DEFERRED):
         batch.set_tiling(tw, th, cps)
 
 

@@ -58,12 +58,29 @@ __device__ __forceinline__ int block_scenario(const uint32_t *__restrict__ prefi
     return lo;
 }
 
+// Brings the fetched values of the available frame neighbours (tv[i], with
+// stamps aux[i]) up to step `now`: fl(v * q) once per missed step, the
+// neighbours' evaporation chains interleaved.
+__device__ __forceinline__ void catch_up_frame(float (&tv)[9], const uint32_t (&aux)[9],
+                                               unsigned avail, uint32_t now, float q)
+{
+    uint32_t age[9], most = 0;
+#pragma unroll
+    for (int i = 2; i <= 8; ++i) {
+        age[i] = (avail & (1u << i)) ? (now - aux[i]) & 255u : 0u;
+        most = age[i] > most ? age[i] : most;
+    }
+    for (uint32_t k = 0; k < most; ++k) {
+#pragma unroll
+        for (int i = 2; i <= 8; ++i)
+            if (k < age[i]) tv[i] = __fmul_rn(tv[i], q);
+    }
+}
+
 // Own-group pheromone of a blocked agent's neighbours, loaded together with
 // its occupancy before it was known whether the forward cell is free (the
 // blocked agents then skip a dependent round of loads): v[i] and, for the
 // deferred step, stamp[i] of frame neighbour i (zero outside the grid).
-// finish() brings deferred values up to step `now`, the neighbours'
-// evaporation chains interleaved.
 struct PrefetchedTau {
     const float *v;
     const uint8_t *stamp;  // nullptr: the values are current
@@ -77,18 +94,29 @@ struct PrefetchedTau {
     __device__ __forceinline__ void finish(float (&tv)[9], const uint32_t (&aux)[9],
                                            unsigned avail) const
     {
-        if (!stamp) return;
-        uint32_t age[9], most = 0;
-#pragma unroll
-        for (int i = 2; i <= 8; ++i) {
-            age[i] = (avail & (1u << i)) ? (now - aux[i]) & 255u : 0u;
-            most = age[i] > most ? age[i] : most;
-        }
-        for (uint32_t k = 0; k < most; ++k) {
-#pragma unroll
-            for (int i = 2; i <= 8; ++i)
-                if (k < age[i]) tv[i] = __fmul_rn(tv[i], q);
-        }
+        if (stamp) catch_up_frame(tv, aux, avail, now, q);
+    }
+};
+
+// The same read from the planes once the agent is known to be blocked: c and
+// sc point at the agent's own cell of its group's plane and of the stamps
+// (nullptr: the values are current).
+struct GlobalTau {
+    const float *c;
+    const uint8_t *sc;
+    int stride;
+    uint32_t now;
+    float q;
+    __device__ __forceinline__ float fetch(int, int code, uint32_t &aux) const
+    {
+        const int off = kCodeDY[code] * stride + kCodeDX[code];
+        aux = sc ? __ldg(sc + off) : 0u;
+        return __ldg(c + off);
+    }
+    __device__ __forceinline__ void finish(float (&tv)[9], const uint32_t (&aux)[9],
+                                           unsigned avail) const
+    {
+        if (sc) catch_up_frame(tv, aux, avail, now, q);
     }
 };
 
@@ -139,11 +167,16 @@ struct BlockedAgent {
 // and, at the next step's proposals, in the plane of the step it moved in
 // (no one writes that plane then); a claimed cell always receives its
 // winner, whose later overwrite or clear removes the flag.
+//
+// prefetch (a launch-wide choice): load every agent's neighbour pheromone
+// with its occupancy, which shortens the blocked agents' chain of dependent
+// loads when the launch's agents fit in one resident wave (latency-bound);
+// without it only the blocked agents load theirs, in the compacted pass,
+// which spends far fewer loads when a launch carries millions of agents
+// (throughput-bound).
 template <bool Deferred>
-__device__ __forceinline__ void propose_block(const ScenarioDesc &d, uint32_t lb, uint64_t t);
-
-template <bool Deferred>
-__device__ __forceinline__ void propose_block(const ScenarioDesc &d, uint32_t lb, uint64_t t)
+__device__ __forceinline__ void propose_block(const ScenarioDesc &d, uint32_t lb, uint64_t t,
+                                              bool prefetch)
 {
     __shared__ BlockedAgent blocked[kAgentBlock];
     __shared__ uint32_t warp_base[kAgentBlock / 32 + 1];
@@ -165,7 +198,7 @@ __device__ __forceinline__ void propose_block(const ScenarioDesc &d, uint32_t lb
         const uint8_t *occ = d.occ[0];
         const float *tp = d.tau[g == 2 ? 1 : 0][Deferred ? 0 : p];
         const int side = g - 1;
-        if (tp) {
+        if (tp && prefetch) {
 #pragma unroll
             for (int i = 1; i <= 8; ++i) {
                 const int code = kFrameCode[side][i];
@@ -207,7 +240,7 @@ __device__ __forceinline__ void propose_block(const ScenarioDesc &d, uint32_t lb
     __syncthreads();
     if (is_blocked) {
         BlockedAgent &e = blocked[warp_base[warp] + __popc(ballot & ((1u << lane) - 1u))];
-        if (d.tau[0][0]) {
+        if (d.tau[0][0] && prefetch) {
 #pragma unroll
             for (int i = 1; i <= 8; ++i) {
                 e.v[i] = pre[i];
@@ -224,10 +257,18 @@ __device__ __forceinline__ void propose_block(const ScenarioDesc &d, uint32_t lb
     if (threadIdx.x < nb) {
         const BlockedAgent &e = blocked[threadIdx.x];
         const RuleParams rp{d.model, d.alpha, d.beta, d.lem_scale};
-        const int code = choose_blocked(e.avail, (int)e.g - 1,
-                                        PrefetchedTau{e.v, Deferred ? e.stamp : nullptr,
-                                                      (uint32_t)t, d.q},
-                                        (uint64_t)e.cell, t, d.seed, rp);
+        int code;
+        if (prefetch || !d.tau[0][0]) {
+            code = choose_blocked(e.avail, (int)e.g - 1,
+                                  PrefetchedTau{e.v, Deferred ? e.stamp : nullptr, (uint32_t)t, d.q},
+                                  (uint64_t)e.cell, t, d.seed, rp);
+        } else {
+            const float *tp = d.tau[e.g == 2 ? 1 : 0][Deferred ? 0 : p] + e.cell;
+            code = choose_blocked(e.avail, (int)e.g - 1,
+                                  GlobalTau{tp, Deferred ? d.stamp + e.cell : nullptr, W,
+                                            (uint32_t)t, d.q},
+                                  (uint64_t)e.cell, t, d.seed, rp);
+        }
         d.codes[p][e.cell] = (uint8_t)code;
         if (code) d.codes[p][(int64_t)e.cell + (int64_t)kCodeDY[code] * W + kCodeDX[code]] = kClaimed;
         d.acode[e.id] = (uint8_t)(code | (e.g << 4));
@@ -285,7 +326,7 @@ __device__ __forceinline__ void stream_block(const ScenarioDesc *__restrict__ de
 __global__ void __launch_bounds__(kAgentBlock, 6)
 agent_stage1_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__restrict__ cell_prefix,
                     const uint32_t *__restrict__ agent_prefix, int n_scen, uint32_t cell_blocks,
-                    uint32_t agent_blocks, uint32_t front)
+                    uint32_t agent_blocks, uint32_t front, int prefetch)
 {
     // The state at t is the previous step's output: wait for it, then let
     // the resolution kernel be scheduled (it waits for this one).
@@ -329,7 +370,7 @@ agent_stage1_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__re
     } else {
         const int s = block_scenario(agent_prefix, n_scen, b);
         const ScenarioDesc &d = descs[s];
-        propose_block<false>(d, b - __ldg(agent_prefix + s), d.step);
+        propose_block<false>(d, b - __ldg(agent_prefix + s), d.step, prefetch != 0);
     }
 }
 
@@ -432,24 +473,42 @@ __device__ __forceinline__ void resolve_load_code(const ScenarioDesc &d, Resolve
     r.g = ac >> 4;
 }
 
-// Claim mask of target cell (tx, ty), gathered from its eight neighbours'
-// codes in the step's code plane (bit j: the neighbour at scan offset j
-// proposed the target, i.e. holds code 8 - j; no atomics, Sec. IV.d).
-// cp points at the target's byte of the plane.
-__device__ __forceinline__ uint32_t gather_claims(const uint8_t *cp, int W, int H, int tx, int ty)
+// Claim mask of target cell (tx, ty) (linear index target), gathered from
+// its eight neighbours' codes in the step's code plane (bit j: the
+// neighbour at scan offset j proposed the target, i.e. holds code 8 - j; no
+// atomics, Sec. IV.d).  Each of the three rows is read with one or two
+// aligned 8-byte loads (the plane holds a multiple of 256 cells, so an
+// aligned word inside it never ends past it).
+__device__ __forceinline__ uint32_t gather_claims(const uint8_t *__restrict__ codes, int W, int H,
+                                                  int64_t target, int tx, int ty)
 {
-    int v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        // scan offset j: (-1,-1) (0,-1) (1,-1) (-1,0) (1,0) (-1,1) (0,1) (1,1)
-        const int ox = j < 3 ? j - 1 : j < 5 ? 2 * j - 7 : j - 6;
-        const int oy = j < 3 ? -1 : j < 5 ? 0 : 1;
-        const bool inside = (unsigned)(tx + ox) < (unsigned)W && (unsigned)(ty + oy) < (unsigned)H;
-        v[j] = inside ? (int)__ldg(cp + (int64_t)oy * W + ox) : 0;
-    }
+    const int64_t cells = (int64_t)W * H;
+    const unsigned long long *w = reinterpret_cast<const unsigned long long *>(codes);
     uint32_t m = 0;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) m |= (v[j] == 8 - j ? 1u : 0u) << j;
+    for (int oy = -1; oy <= 1; ++oy) {
+        if ((unsigned)(ty + oy) >= (unsigned)H) continue;
+        const int64_t base = target + (int64_t)oy * W - 1;  // cell (tx - 1, ty + oy)
+        const int64_t lo = (base < 0 ? 0 : base) & ~(int64_t)7;
+        const int off = (int)(base - lo);  // -1 only for tx = 0 in row 0
+        const unsigned long long w0 = __ldg(w + lo / 8);
+        const unsigned long long w1 = off > 5 && lo + 8 < cells ? __ldg(w + lo / 8 + 1) : 0ull;
+        // bytes off, off + 1, off + 2 of w1:w0: the left, middle, right cell
+        const auto byte_at = [&](int b) -> uint32_t {
+            return b < 0 ? 0u : b < 8 ? (uint32_t)(w0 >> (8 * b)) & 255u
+                                      : (uint32_t)(w1 >> (8 * (b - 8))) & 255u;
+        };
+        const uint32_t left = tx > 0 ? byte_at(off) : 0u;
+        const uint32_t mid = byte_at(off + 1);
+        const uint32_t right = tx + 1 < W ? byte_at(off + 2) : 0u;
+        if (oy < 0) {
+            m |= (left == 8u ? 1u : 0u) | (mid == 7u ? 2u : 0u) | (right == 6u ? 4u : 0u);
+        } else if (oy == 0) {
+            m |= (left == 5u ? 8u : 0u) | (right == 4u ? 16u : 0u);
+        } else {
+            m |= (left == 3u ? 32u : 0u) | (mid == 2u ? 64u : 0u) | (right == 1u ? 128u : 0u);
+        }
+    }
     return m;
 }
 
@@ -467,7 +526,7 @@ __device__ __forceinline__ void resolve_load_target(const ScenarioDesc &d, uint6
     r.late = (uint64_t)r.target / kCellBlock >= late_from;
     r.tau_t = d.model == 1 ? __ldg(d.tau[r.g == 2 ? 1 : 0][p] + r.target) : 0.0f;
     r.tau_o = d.model == 1 && r.late ? __ldg(d.tau[r.g == 2 ? 0 : 1][p] + r.target) : 0.0f;
-    r.mask = gather_claims(d.codes[p] + r.target, W, H, tx, ty);
+    r.mask = gather_claims(d.codes[p], W, H, r.target, tx, ty);
 }
 
 // The winner of the target (Sec. IV.d) and, if it is this agent, its move.
@@ -645,7 +704,8 @@ __device__ __forceinline__ float evaporate_n(float v, uint32_t age, float q)
 // First kernel of the deferred step: the proposals only.
 __global__ void __launch_bounds__(kAgentBlock)
 deferred_stage1_kernel(const ScenarioDesc *__restrict__ descs,
-                       const uint32_t *__restrict__ agent_prefix, int n_scen, uint32_t agent_blocks)
+                       const uint32_t *__restrict__ agent_prefix, int n_scen, uint32_t agent_blocks,
+                       int prefetch)
 {
     pdl_wait();
     pdl_trigger();
@@ -653,7 +713,7 @@ deferred_stage1_kernel(const ScenarioDesc *__restrict__ descs,
     if (b >= agent_blocks) return;
     const int s = block_scenario(agent_prefix, n_scen, b);
     const ScenarioDesc &d = descs[s];
-    propose_block<true>(d, b - __ldg(agent_prefix + s), d.step);
+    propose_block<true>(d, b - __ldg(agent_prefix + s), d.step, prefetch != 0);
 }
 
 // Rolling refresh of cell block b of scenario d at step t: every unclaimed
@@ -726,7 +786,7 @@ deferred_resolve_kernel(const ScenarioDesc *__restrict__ descs,
                         const uint32_t *__restrict__ agent_prefix,
                         const uint32_t *__restrict__ cell_prefix,
                         const uint32_t *__restrict__ slice_prefix, int n_scen,
-                        uint32_t agent_blocks, ActivityCtl *__restrict__ ctl)
+                        uint32_t agent_blocks, ActivityCtl *__restrict__ ctl, int prefetch)
 {
     unsigned int ticket = 0;
     if (blockIdx.x >= agent_blocks) {
@@ -756,10 +816,13 @@ deferred_resolve_kernel(const ScenarioDesc *__restrict__ descs,
         const bool aco = d.model == 1;
         const int W = d.W, H = d.H;
         Resolve r;
-        // Before the wait for the proposals: the agent's own entries, then
-        // both groups' values and the stamps of its eight neighbours (the
-        // first kernel writes none of them): whichever neighbour it proposed,
-        // its target's are at hand after the wait.
+        // Before the wait for the proposals: the agent's own entries and, with
+        // `prefetch` (latency-bound launches), both groups' values and the
+        // stamps of its eight neighbours (the first kernel writes none of
+        // them): whichever neighbour it proposed, its target's are at hand
+        // after the wait.  Without it the target's are loaded with its
+        // neighbours' codes (throughput-bound launches: 3 loads per agent
+        // instead of 24).
         float va[8], vb[8];
         uint32_t st[8];
         int x = 0, y = 0;
@@ -768,16 +831,18 @@ deferred_resolve_kernel(const ScenarioDesc *__restrict__ descs,
             x = (int)(r.cell % (uint32_t)W);
             y = (int)(r.cell / (uint32_t)W);
         }
+        if (prefetch) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int ox = j < 3 ? j - 1 : j < 5 ? 2 * j - 7 : j - 6;  // scan offset j
-            const int oy = j < 3 ? -1 : j < 5 ? 0 : 1;
-            const bool ok = live && aco && (unsigned)(x + ox) < (unsigned)W &&
-                            (unsigned)(y + oy) < (unsigned)H;
-            const int64_t off = (int64_t)r.cell + (int64_t)oy * W + ox;
-            va[j] = ok ? ld_nc_f32(d.tau[0][0] + off) : 0.0f;
-            vb[j] = ok ? ld_nc_f32(d.tau[1][0] + off) : 0.0f;
-            st[j] = ok ? ld_nc_u8(d.stamp + off) : 0u;
+            for (int j = 0; j < 8; ++j) {
+                const int ox = j < 3 ? j - 1 : j < 5 ? 2 * j - 7 : j - 6;  // scan offset j
+                const int oy = j < 3 ? -1 : j < 5 ? 0 : 1;
+                const bool ok = live && aco && (unsigned)(x + ox) < (unsigned)W &&
+                                (unsigned)(y + oy) < (unsigned)H;
+                const int64_t off = (int64_t)r.cell + (int64_t)oy * W + ox;
+                va[j] = ok ? ld_nc_f32(d.tau[0][0] + off) : 0.0f;
+                vb[j] = ok ? ld_nc_f32(d.tau[1][0] + off) : 0.0f;
+                st[j] = ok ? ld_nc_u8(d.stamp + off) : 0u;
+            }
         }
         pdl_wait();  // proposals complete
         pdl_trigger();
@@ -793,7 +858,14 @@ deferred_resolve_kernel(const ScenarioDesc *__restrict__ descs,
             const int dx = kCodeDX[r.code], dy = kCodeDY[r.code];
             r.target = (int64_t)r.cell + (int64_t)dy * W + dx;
             const int tx = x + dx;
-            r.mask = gather_claims(d.codes[(int)(t & 1)] + r.target, W, H, tx, y + dy);
+            float ta = 0.0f, tb = 0.0f;
+            uint32_t ts = 0;
+            if (aco && !prefetch) {
+                ta = __ldg(d.tau[0][0] + r.target);
+                tb = __ldg(d.tau[1][0] + r.target);
+                ts = __ldg(d.stamp + r.target);
+            }
+            r.mask = gather_claims(d.codes[(int)(t & 1)], W, H, r.target, tx, y + dy);
             const uint32_t k = (uint32_t)__popc(r.mask);
             const uint32_t mine = 8u - (uint32_t)r.code;
             const uint32_t win =
@@ -821,11 +893,11 @@ deferred_resolve_kernel(const ScenarioDesc *__restrict__ descs,
                     // the target is this agent's neighbour at scan offset
                     // code - 1: its values at t (both groups' chains
                     // interleaved), then step t's evaporation and the deposit
-                    float ta = 0.0f, tb = 0.0f;
-                    uint32_t ts = 0;
+                    if (prefetch) {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        if (j == r.code - 1) { ta = va[j]; tb = vb[j]; ts = st[j]; }
+                        for (int j = 0; j < 8; ++j)
+                            if (j == r.code - 1) { ta = va[j]; tb = vb[j]; ts = st[j]; }
+                    }
                     const float q = d.q;
                     const uint32_t age = (((uint32_t)t - ts) & 255u) + 1u;
                     for (uint32_t i = 0; i < age; ++i) {
@@ -927,6 +999,18 @@ static uint32_t resolve_wave()
     return resident_wave(agent_resolve_kernel, cache);
 }
 
+static uint32_t deferred_stage1_wave()
+{
+    static std::atomic<uint32_t> cache[kMaxDevices];
+    return resident_wave(deferred_stage1_kernel, cache);
+}
+
+static uint32_t deferred_resolve_wave()
+{
+    static std::atomic<uint32_t> cache[kMaxDevices];
+    return resident_wave(deferred_resolve_kernel, cache);
+}
+
 // Cell blocks of a step evaporated in the resolution kernel: the free part
 // of one resident wave of that kernel, at most all but one cell block (the
 // first kernel must run whenever there are cell blocks: the resolution
@@ -955,10 +1039,12 @@ cudaError_t launch_agent_step(const ScenarioDesc *d_descs, const uint32_t *d_cel
         const uint32_t wave = stage1_wave();
         const uint32_t front = agent_blocks < wave ? agent_blocks : wave;
         const uint32_t c1 = cell_blocks - late;
+        // speculative pheromone loads only while the agents fit in one wave
+        const int prefetch = agent_blocks <= wave;
         if (c1 + agent_blocks) {
             cudaError_t e = launch_pdl(agent_stage1_kernel, c1 + agent_blocks,
                                        (unsigned)kAgentBlock, stream, d_descs, d_cell_prefix,
-                                       d_agent_prefix, n, c1, agent_blocks, front);
+                                       d_agent_prefix, n, c1, agent_blocks, front, prefetch);
             if (e != cudaSuccess) return e;
         }
     }
@@ -979,13 +1065,17 @@ cudaError_t launch_deferred_step(const ScenarioDesc *d_descs, const uint32_t *d_
     if (n <= 0) return cudaSuccess;
     // the first kernel runs even with no agent: the refresh CTAs' loads
     // before their wait rely on it having waited for the previous step
+    // speculative loads only while each kernel's CTAs fit in one resident
+    // wave (latency-bound); a launch with more agents is throughput-bound
+    const int pre1 = agent_blocks <= deferred_stage1_wave();
     cudaError_t e = launch_pdl(deferred_stage1_kernel, agent_blocks > 0 ? agent_blocks : 1u,
                                (unsigned)kAgentBlock, stream, d_descs, d_agent_prefix, n,
-                               agent_blocks);
+                               agent_blocks, pre1);
     if (e != cudaSuccess) return e;
     const uint32_t g = agent_blocks + slices > 0 ? agent_blocks + slices : 1u;
+    const int pre2 = g <= deferred_resolve_wave();
     return launch_pdl(deferred_resolve_kernel, g, (unsigned)kAgentBlock, stream, d_descs,
-                      d_agent_prefix, d_cell_prefix, d_slice_prefix, n, agent_blocks, ctl);
+                      d_agent_prefix, d_cell_prefix, d_slice_prefix, n, agent_blocks, ctl, pre2);
 }
 
 uint32_t deferred_slices(uint32_t cell_blocks)
@@ -1004,8 +1094,10 @@ cudaError_t launch_deferred_catch_up(const ScenarioDesc *d_desc, int cells, cuda
 
 cudaError_t launch_build_pos(const ScenarioDesc *d_desc, int cells, int plane, cudaStream_t stream)
 {
-    (void)stage1_wave();  // the step's occupancy queries, outside any capture
+    (void)stage1_wave();  // the steps' occupancy queries, outside any capture
     (void)resolve_wave();
+    (void)deferred_stage1_wave();
+    (void)deferred_resolve_wave();
     int blocks = (cells + 255) / 256;
     if (blocks > 1024) blocks = 1024;
     if (blocks < 1) blocks = 1;
