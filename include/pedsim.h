@@ -336,8 +336,10 @@ const char *sim_pool_last_error(const pool_t *pl);
  * from different threads -- race and must be serialised by the caller.  The
  * first call on a device looks up the array's device address (with that
  * device current) and caches it; make that first call before any stream
- * capture.  Returns PEDSIM_EINVAL for invalid parameters or sizes, NULL or
- * aliased buffers, PEDSIM_ECUDA when a launch fails.                         */
+ * capture; the cached address belongs to the device's context and must not
+ * be used after a cudaDeviceReset of that device.  Returns PEDSIM_EINVAL for
+ * invalid parameters or sizes, NULL buffers or occupancy buffers that share
+ * any byte, PEDSIM_ECUDA when a launch fails.                                 */
 int sim_step_noalloc(int W, int H, const sim_params *p, uint64_t seed, uint64_t step,
                      const uint8_t *occ_in, uint8_t *occ_out, uint32_t *ids,
                      const float *tauA_in, const float *tauB_in, float *tauA_out,

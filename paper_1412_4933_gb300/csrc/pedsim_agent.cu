@@ -484,6 +484,8 @@ __device__ __forceinline__ uint32_t gather_claims(const uint8_t *__restrict__ co
 {
     const int64_t cells = (int64_t)W * H;
     const unsigned long long *w = reinterpret_cast<const unsigned long long *>(codes);
+    // edge masks: no left neighbour in column 0, no right one in column W-1
+    const uint32_t keep = (tx > 0 ? 0x0000FFu : 0u) | 0x00FF00u | (tx + 1 < W ? 0xFF0000u : 0u);
     uint32_t m = 0;
 #pragma unroll
     for (int oy = -1; oy <= 1; ++oy) {
@@ -493,21 +495,16 @@ __device__ __forceinline__ uint32_t gather_claims(const uint8_t *__restrict__ co
         const int off = (int)(base - lo);  // -1 only for tx = 0 in row 0
         const unsigned long long w0 = __ldg(w + lo / 8);
         const unsigned long long w1 = off > 5 && lo + 8 < cells ? __ldg(w + lo / 8 + 1) : 0ull;
-        // bytes off, off + 1, off + 2 of w1:w0: the left, middle, right cell
-        const auto byte_at = [&](int b) -> uint32_t {
-            return b < 0 ? 0u : b < 8 ? (uint32_t)(w0 >> (8 * b)) & 255u
-                                      : (uint32_t)(w1 >> (8 * (b - 8))) & 255u;
-        };
-        const uint32_t left = tx > 0 ? byte_at(off) : 0u;
-        const uint32_t mid = byte_at(off + 1);
-        const uint32_t right = tx + 1 < W ? byte_at(off + 2) : 0u;
-        if (oy < 0) {
-            m |= (left == 8u ? 1u : 0u) | (mid == 7u ? 2u : 0u) | (right == 6u ? 4u : 0u);
-        } else if (oy == 0) {
-            m |= (left == 5u ? 8u : 0u) | (right == 4u ? 16u : 0u);
-        } else {
-            m |= (left == 3u ? 32u : 0u) | (mid == 2u ? 64u : 0u) | (right == 1u ? 128u : 0u);
-        }
+        // bytes 0, 1, 2 of v: the left, middle and right cell of the row
+        const unsigned long long v =
+            off < 0 ? w0 << 8 : off == 0 ? w0 : (w0 >> (8 * off)) | (w1 << (64 - 8 * off));
+        // codes of the moves into the target from the row's left, middle and
+        // right cell (the target itself, in the middle of its own row, can
+        // hold no code: 0xFF never matches)
+        const uint32_t pat = oy < 0 ? 0x00060708u : oy == 0 ? 0x0004FF05u : 0x00010203u;
+        const uint32_t eq = __vcmpeq4((uint32_t)v & keep & 0x00FFFFFFu, pat) & 0x00010101u;
+        const uint32_t bits = (eq & 1u) | ((eq >> 7) & 2u) | ((eq >> 14) & 4u);
+        m |= oy < 0 ? bits : oy == 0 ? ((bits & 1u) << 3) | ((bits & 4u) << 2) : bits << 5;
     }
     return m;
 }
@@ -701,8 +698,9 @@ __device__ __forceinline__ float evaporate_n(float v, uint32_t age, float q)
     return v;
 }
 
-// First kernel of the deferred step: the proposals only.
-__global__ void __launch_bounds__(kAgentBlock)
+// First kernel of the deferred step: the proposals only (six resident CTAs
+// per SM, as the agent step's first kernel).
+__global__ void __launch_bounds__(kAgentBlock, 6)
 deferred_stage1_kernel(const ScenarioDesc *__restrict__ descs,
                        const uint32_t *__restrict__ agent_prefix, int n_scen, uint32_t agent_blocks,
                        int prefetch)

@@ -147,24 +147,41 @@ noalloc_resolve_kernel(const __grid_constant__ NoAllocStep a, const uint8_t *__r
 // device current (host code cannot use the symbol itself: in host code its
 // name stands for a host-side shadow, not device memory).
 constexpr int kMaxDevices = 64;
+// Per device, looked up once with that device current: the array's device
+// address and the grid cap of the grid-stride kernels (16 CTAs per SM).  A
+// cudaDeviceReset destroys the context these belong to; the library does not
+// notice one, so the cached address must not be used after a reset.
 std::mutex g_addr_mutex;
 uint8_t *g_addr[kMaxDevices] = {};
+unsigned g_max_blocks[kMaxDevices] = {};
 
-int scratch_address(uint8_t **out)
+int scratch_address(uint8_t **out, unsigned *max_blocks)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PEDSIM_ECUDA;
     std::lock_guard<std::mutex> lock(g_addr_mutex);
     if (!g_addr[dev]) {
         void *ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_noalloc_prop) != cudaSuccess || !ptr) {
+        int sms = 0;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_prop) != cudaSuccess || !ptr ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            sms <= 0) {
             cudaGetLastError();
             return PEDSIM_ECUDA;
         }
+        g_max_blocks[dev] = 16u * (unsigned)sms;
         g_addr[dev] = static_cast<uint8_t *>(ptr);
     }
     *out = g_addr[dev];
+    *max_blocks = g_max_blocks[dev];
     return PEDSIM_OK;
+}
+
+// [a, a + n) and [b, b + n) share a byte.
+bool overlap(const void *a, const void *b, size_t n)
+{
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + n && y < x + n;
 }
 
 }  // namespace
@@ -181,11 +198,16 @@ extern "C" int sim_step_noalloc(int W, int H, const sim_params *p, uint64_t seed
     if (sim_validate(W, H, p) != PEDSIM_OK) return PEDSIM_EINVAL;
     if ((size_t)W * (size_t)H > kNoAllocMaxCells) return PEDSIM_EINVAL;
     const bool aco = p->model == PEDSIM_ACO;
-    if (!occ_in || !occ_out || !ids || !arrival || occ_in == occ_out) return PEDSIM_EINVAL;
+    const size_t cells = (size_t)W * H;
+    if (!occ_in || !occ_out || !ids || !arrival) return PEDSIM_EINVAL;
+    // the resolution pass reads occ_in around every cell while it writes
+    // occ_out: the two may not share a byte
+    if (overlap(occ_in, occ_out, cells)) return PEDSIM_EINVAL;
     if (aco && (!tauA_in || !tauB_in || !tauA_out || !tauB_out)) return PEDSIM_EINVAL;
     if (aco && p->deposit_mode == 1 && !tour) return PEDSIM_EINVAL;
     uint8_t *prop = nullptr;
-    const int rc = scratch_address(&prop);
+    unsigned max_blocks = 0;
+    const int rc = scratch_address(&prop, &max_blocks);
     if (rc != PEDSIM_OK) return rc;
 
     NoAllocStep a{};
@@ -213,9 +235,8 @@ extern "C" int sim_step_noalloc(int W, int H, const sim_params *p, uint64_t seed
     a.counters = counters;
 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const size_t cells = (size_t)W * H;
     size_t blocks = (cells + kNaThreads - 1) / kNaThreads;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > max_blocks) blocks = max_blocks;
     noalloc_propose_kernel<<<(unsigned)blocks, kNaThreads, 0, st>>>(a, prop);
     if (cudaGetLastError() != cudaSuccess) return PEDSIM_ECUDA;
     noalloc_resolve_kernel<<<(unsigned)blocks, kNaThreads, 0, st>>>(a, prop);

@@ -25,6 +25,10 @@ CASES = [
     WL.Scenario(176, 80, WL.ACO, 1500, 30, 23, 2, rho=0.1, name="aco_176x80"),
     WL.Scenario(128, 64, WL.LEM, 900, 20, 5, 2, name="lem_128x64"),
     WL.Scenario(96, 48, WL.ACO, 600, 24, 9, 2, rho=0.03, deposit_mode=1, name="aco_inverse_tour"),
+    # more cells than one pass of the grid-stride kernels covers (16 CTAs of
+    # 256 threads per SM: 622,592 cells on 152 SMs)
+    WL.Scenario(1024, 1024, WL.LEM, 60000, 64, 41, 2, name="lem_1024x1024"),
+    WL.Scenario(1024, 1024, WL.ACO, 60000, 64, 42, 2, rho=0.05, name="aco_1024x1024"),
 ]
 
 
@@ -81,6 +85,17 @@ def test_noalloc_rejects_oversize_grids_and_aliased_buffers():
     big = P.make_params(model=P.LEM, n_per_side=10, band_cols=16)
     assert P.step_noalloc(8192, 4096, big, 1, 0, small, small[1:], words, arrival=words) == P.EINVAL
     assert P.NOALLOC_MAX_CELLS == 1 << 24
-    # occupancy in and out must be distinct buffers
+    # occupancy in and out must not share a byte: the same buffer, or one
+    # starting inside the other, is rejected
     prm = P.make_params(model=P.LEM, n_per_side=10, band_cols=4)
-    assert P.step_noalloc(16, 16, prm, 1, 0, small, small, words, arrival=words) == P.EINVAL
+    occ = torch.zeros(512, dtype=torch.uint8, device="cuda")
+    assert P.step_noalloc(16, 16, prm, 1, 0, occ, occ, words, arrival=words) == P.EINVAL
+    assert P.step_noalloc(16, 16, prm, 1, 0, occ, occ[100:], words, arrival=words) == P.EINVAL
+    assert P.step_noalloc(16, 16, prm, 1, 0, occ[100:], occ, words, arrival=words) == P.EINVAL
+    # adjacent, disjoint halves of one buffer are accepted (a real step on
+    # an empty 16 x 16 grid with buffers of the full sizes)
+    ids = torch.zeros(256, dtype=torch.int32, device="cuda")
+    arrival = torch.zeros(2 * 10 + 1, dtype=torch.int32, device="cuda")
+    assert P.step_noalloc(16, 16, prm, 1, 0, occ[:256], occ[256:], ids, arrival=arrival) == P.OK
+    torch.cuda.synchronize()
+    assert int(occ[256:].sum()) == 0
