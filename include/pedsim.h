@@ -305,6 +305,47 @@ void sim_pool_destroy(pool_t *pl);
 const char *sim_pool_last_error(const pool_t *pl);
 
 /* ------------------------------------------------------------------------ */
+/* Domain decomposition: one step of a column strip of a larger grid.        */
+/* ------------------------------------------------------------------------ */
+/* A W_global x H grid split into strips of columns (each on its own device
+ * or stream) advances by one sim_step_strip call per strip and step, with
+ * the strips' halos refreshed from their neighbours' interiors in between
+ * (paper_1412_4933_gb300/domain.py does both).  The strip's buffers hold its
+ * local columns: interior_lo .. interior_hi-1 are its own, the others (at most
+ * three on each side, more are allowed but unused) a halo copied from the
+ * neighbouring strips.  The state of a cell after one step depends only on
+ * cells at most three columns away (Sec. IV.b-d: a claimant's proposal needs
+ * its 3 x 3 neighbourhood, an agent's departure its target's other
+ * claimants), so with three halo columns the interior comes out bit for bit
+ * as in sim_step on the whole grid; the halo's own results are to be
+ * replaced by the next exchange.  Random numbers, the goal edge and the
+ * crossing line use global coordinates (x0 = global column of local column
+ * 0); neighbours beyond the strip's local columns count as unavailable.
+ *   W, H            local width (interior + halos) and height (= the grid's)
+ *   x0, W_global    global column of local column 0; width of the whole grid
+ *   interior_lo/hi  the strip's own local columns [lo, hi); only events whose
+ *                   target cell lies there are added to `counters`
+ *   p, seed, step   the whole grid's parameters (validated against
+ *                   W_global x H), its seed and the step index being taken
+ *   occ_in/occ_out, ids, tau*_in/out, arrival, tour, counters
+ *                   as in sim_step_noalloc, all device memory of the caller,
+ *                   W x H local cells (per-agent arrays: 2N+1 entries; an
+ *                   agent's entries must be current whenever it stands in the
+ *                   strip's local columns)
+ *   scratch         device uint8 W*H owned by the caller (the proposal plane)
+ *   stream          cudaStream_t, NULL = the legacy default stream
+ * Asynchronous on the stream; allocates nothing.  PEDSIM_EINVAL for invalid
+ * parameters, columns outside the grid, NULL buffers, or occ_in, occ_out
+ * and scratch sharing bytes; PEDSIM_ECUDA when a launch fails.  The paper
+ * runs one grid on one GPU (Sec. V); this call serves the decomposition of
+ * one grid over several devices, which the paper does not address.          */
+int sim_step_strip(int W, int H, int x0, int W_global, int interior_lo, int interior_hi,
+                   const sim_params *p, uint64_t seed, uint64_t step, const uint8_t *occ_in,
+                   uint8_t *occ_out, uint32_t *ids, const float *tauA_in, const float *tauB_in,
+                   float *tauA_out, float *tauB_out, uint32_t *arrival, float *tour,
+                   uint8_t *scratch, unsigned long long *counters, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Allocation-free step.  The paper has no counterpart: this entry point     */
 /* exists for callers that cannot let a library allocate device memory while */
 /* they run -- applications that reserve all device memory up front under a  */

@@ -20,7 +20,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpedsim.so")
 
-SOURCES = ["pedsim_kernels.cu", "pedsim_agent.cu", "pedsim_host.cpp", "pedsim_noalloc.cu"]
+SOURCES = ["pedsim_kernels.cu", "pedsim_agent.cu", "pedsim_host.cpp", "pedsim_noalloc.cu",
+           "pedsim_strip.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -93,6 +93,9 @@ _SIGS = {
     "sim_pool_last_error": (C.c_char_p, [_P]),
     "sim_step_noalloc": (C.c_int, [C.c_int, C.c_int, C.POINTER(SimParams), C.c_uint64, C.c_uint64,
                                    _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "sim_step_strip": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                 C.POINTER(SimParams), C.c_uint64, C.c_uint64,
+                                 _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -402,6 +405,22 @@ def step_noalloc(W, H, params: SimParams, seed: int, step: int, occ_in, occ_out,
     return int(_lib.sim_step_noalloc(W, H, C.byref(params), seed, step, ptr(occ_in), ptr(occ_out),
                                      ptr(ids), ptr(tauA_in), ptr(tauB_in), ptr(tauA_out),
                                      ptr(tauB_out), ptr(arrival), ptr(tour), ptr(counters), stream))
+
+
+def step_strip(W, H, x0, W_global, interior_lo, interior_hi, params: SimParams, seed: int,
+               step: int, occ_in, occ_out, ids, tauA_in, tauB_in, tauA_out, tauB_out, arrival,
+               tour, scratch, counters=None, stream=None) -> int:
+    """One step of a column strip of a W_global x H grid on caller-owned
+    device tensors (``sim_step_strip``); returns the C status code."""
+    ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+    if stream is None:
+        stream = _default_stream()
+    elif not isinstance(stream, C.c_void_p):
+        stream = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    return int(_lib.sim_step_strip(W, H, x0, W_global, interior_lo, interior_hi, C.byref(params),
+                                   seed, step, ptr(occ_in), ptr(occ_out), ptr(ids), ptr(tauA_in),
+                                   ptr(tauB_in), ptr(tauA_out), ptr(tauB_out), ptr(arrival),
+                                   ptr(tour), ptr(scratch), ptr(counters), stream))
 
 
 def exported_symbols():
