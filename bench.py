@@ -29,15 +29,22 @@ Also reported on the same line:
   cpu_baseline  the single-threaded CPU oracle on a bounded sample
   e2e           the same metric end to end through the C ABI with host
                 buffers: H2D of the initial state (pinned), the scenario's
-                2000 steps, D2H of the final grid and counters
+                2000 steps, D2H of the final grid and counters (one
+                instance, its state L2-resident across the run; bytes per
+                step = the run's bytes / 2000)
+  deferred_evaporation
+                the same workload and timing with the deferred-evaporation
+                step (per-cell stamps, bit-identical results, 18/32 B per
+                cell-step of dense traffic), reported beside the headline
   steady        steps replayed back to back (CUDA graph), no flush: the
                 simulation's own L2-resident regime
   inputs_larger_than_l2
                 four independent copies of the headline scenario advanced
                 together (inputs 4 x 101 MiB > L2), graph replays timed with
                 one event pair: the cold-L2 step without per-step events
-  batched       256 uneven scenarios x 500 steps in the persistent batched
-                launch, vs one launch per scenario per step
+  batched       256 uneven scenarios x 500 steps in batched launches (the
+                autotuner's configuration), vs the same scenarios and steps
+                run one scenario at a time; algorithmic GB/s beside it
   serving       Poisson request stream through the serving pool: p50/p99
 
 `--impl reference` times the CPU oracle instead (the reference arm).
