@@ -46,14 +46,24 @@ constexpr int kMaxDevices = 64;  // devices whose occupancy is cached
 constexpr uint8_t kClaimed = 0x80;  // code-plane byte of an empty cell some agent proposed
 
 
-// Scenario of work block b (prefix[i] = first block of scenario i).
+// Scenario of work block b (prefix[i] = first block of scenario i, non-
+// decreasing, prefix[0] = 0): the largest i < n with prefix[i] <= b.  A
+// 32-way search by the whole warp (b is the same in every lane): each round
+// the lanes test 32 evenly spaced entries at once, so 256 scenarios take two
+// rounds of loads instead of eight dependent ones.  Every lane of the warp
+// must call it.
 __device__ __forceinline__ int block_scenario(const uint32_t *__restrict__ prefix, int n,
                                               uint32_t b)
 {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(prefix + mid) <= b) lo = mid; else hi = mid - 1;
+    const int lane = (int)(threadIdx.x & 31u);
+    int lo = 0, hi = n;  // the answer lies in [lo, hi)
+    while (hi - lo > 1) {
+        const int step = (hi - lo + 31) >> 5;
+        const int idx = lo + lane * step;
+        const bool ok = idx < hi && __ldg(prefix + idx) <= b;
+        const unsigned m = __ballot_sync(0xffffffffu, ok);  // lane 0 (idx = lo) always holds
+        lo += (31 - __clz((int)m)) * step;
+        hi = min(hi, lo + step);
     }
     return lo;
 }
