@@ -46,6 +46,12 @@ constexpr int kMaxDevices = 64;  // devices whose occupancy is cached
 constexpr uint8_t kClaimed = 0x80;  // code-plane byte of an empty cell some agent proposed
 
 
+// Row of cell c (< 2^31) of scenario d without a divide (see ScenarioDesc).
+__device__ __forceinline__ uint32_t cell_row(const ScenarioDesc &d, uint32_t c)
+{
+    return __umulhi(c, d.w_mul) >> d.w_shr;
+}
+
 // Scenario of work block b (prefix[i] = first block of scenario i, non-
 // decreasing, prefix[0] = 0): the largest i < n with prefix[i] <= b.  A
 // 32-way search by the whole warp (b is the same in every lane): each round
@@ -204,7 +210,8 @@ __device__ __forceinline__ void propose_block(const ScenarioDesc &d, uint32_t lb
         cell = __ldg(d.pos + id);
         const int prev = __ldg(d.acode + id);
         g = prev >> 4 & 3;
-        const int x = (int)(cell % (uint32_t)W), y = (int)(cell / (uint32_t)W);
+        const uint32_t yr = cell_row(d, cell);
+        const int x = (int)(cell - yr * (uint32_t)W), y = (int)yr;
         const uint8_t *occ = d.occ[0];
         const float *tp = d.tau[g == 2 ? 1 : 0][Deferred ? 0 : p];
         const int side = g - 1;
@@ -529,7 +536,8 @@ __device__ __forceinline__ void resolve_load_target(const ScenarioDesc &d, uint6
     const int p = (int)(t & 1);
     const int dx = kCodeDX[r.code], dy = kCodeDY[r.code];
     r.target = (int64_t)r.cell + (int64_t)dy * W + dx;
-    const int tx = (int)(r.cell % (uint32_t)W) + dx, ty = (int)(r.cell / (uint32_t)W) + dy;
+    const uint32_t yr = cell_row(d, r.cell);
+    const int tx = (int)(r.cell - yr * (uint32_t)W) + dx, ty = (int)yr + dy;
     r.late = (uint64_t)r.target / kCellBlock >= late_from;
     r.tau_t = d.model == 1 ? __ldg(d.tau[r.g == 2 ? 1 : 0][p] + r.target) : 0.0f;
     r.tau_o = d.model == 1 && r.late ? __ldg(d.tau[r.g == 2 ? 0 : 1][p] + r.target) : 0.0f;
@@ -548,7 +556,7 @@ __device__ __forceinline__ void resolve_apply(const ScenarioDesc &d, uint64_t t,
     const int p = (int)(t & 1);
     const int g = r.g;
     const int dx = kCodeDX[r.code], dy = kCodeDY[r.code];
-    const int tx = (int)(r.cell % (uint32_t)W) + dx;
+    const int tx = (int)(r.cell - cell_row(d, r.cell) * (uint32_t)W) + dx;
     d.occ[0][r.target] = (uint8_t)g;
     d.occ[0][r.cell] = 0;
     d.codes[p ^ 1][r.cell] = 0;  // its old cell, in the plane of step t + 1
@@ -836,8 +844,8 @@ deferred_resolve_kernel(const ScenarioDesc *__restrict__ descs,
         int x = 0, y = 0;
         if (live) {
             resolve_load_own(d, a, r);
-            x = (int)(r.cell % (uint32_t)W);
-            y = (int)(r.cell / (uint32_t)W);
+            y = (int)cell_row(d, r.cell);
+            x = (int)(r.cell - (uint32_t)y * (uint32_t)W);
         }
         if (prefetch) {
 #pragma unroll

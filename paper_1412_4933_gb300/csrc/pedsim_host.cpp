@@ -259,6 +259,7 @@ int upload_desc(sim_t *s)
     d.deposit = s->p.deposit;
     d.lem_scale = 0x1p-16f / s->p.lem_sigma;
     d.tau0 = s->p.tau0;
+    division_by_width(s->W, &d.w_mul, &d.w_shr);
     d.wait_cycles = s->wait_cycles;
     d.test_flags = s->test_flags;
     const int TWd = s->tile_w, THd = s->tile_h;

@@ -51,6 +51,11 @@ namespace pedsim {
 //                 byte of the step at which the cell's values in tau[g][0]
 //                 are valid (the variant keeps one plane per group, updated
 //                 in place)
+//   w_mul, w_shr  division of a cell index by W without a divide: with
+//                 l = ceil(log2 W), w_mul = floor(2^(31+l) / W) + 1 and
+//                 w_shr = l - 1, floor(c / W) = umulhi(c, w_mul) >> w_shr for
+//                 every c < 2^31 (the round-up method of Granlund and
+//                 Montgomery, 1994: w_mul * W exceeds 2^(31+l) by at most W)
 //   test_flags    failure-detection test hook: with kTestSkipResolveLoads the
 //                 tiled resolution kernel issues none of its TMA loads, so
 //                 its bounded wait runs out and it returns without writing
@@ -88,7 +93,8 @@ struct alignas(128) ScenarioDesc {
     uint32_t test_flags;             // kTestSkipResolveLoads (failure-detection test only)
     uint32_t pad1_;
     uint8_t *stamp;                  // deferred-evaporation stamps (ACO)
-    uint8_t header_pad_[kDescHeaderBytes - 96 - 16 * 8 - 24];
+    uint32_t w_mul, w_shr;           // cell / W = umulhi(cell, w_mul) >> w_shr (cell < 2^31)
+    uint8_t header_pad_[kDescHeaderBytes - 96 - 16 * 8 - 32];
     // TMA tensor maps; boxes follow the variant and tile shape:
     //   tiled two-kernel step: occ (tile_w + 32) x (tile_h + 2), occ_out and
     //   prop_out tile_w x tile_h, prop (tile_w + 32) x (tile_h + 4), tau
@@ -121,6 +127,15 @@ struct ActivityCtl {
     uint32_t n_act[3];
     uint32_t work_nat;  // next work item of the natural-order pass
 };
+// The multiplier and shift of the division by W (see ScenarioDesc).
+inline void division_by_width(int W, uint32_t *mul, uint32_t *shr)
+{
+    uint32_t l = 0;
+    while ((1ull << l) < (unsigned long long)W) ++l;
+    *mul = (uint32_t)(((1ull << (31 + l)) / (unsigned long long)W) + 1ull);
+    *shr = l - 1;
+}
+
 inline size_t activity_bytes(uint32_t total)
 {
     return sizeof(ActivityCtl) + 4 * (3 * (((size_t)total + 31) / 32) + 3 * (size_t)total);

@@ -89,3 +89,29 @@ def test_oracle_and_library_share_no_source():
             assert "import oracle" not in text and "from oracle" not in text, f
     otext = open(os.path.join(ROOT, "oracle", "pedsim_oracle.c")).read()
     assert "#include \"" not in otext
+
+
+def test_division_by_width_multiplier():
+    """The kernels divide cell indices (< 2^31) by the grid width W with a
+    multiplier and a shift computed on the host (round-up method of
+    Granlund and Montgomery): floor(c / W) = umulhi(c, mul) >> shr with
+    l = ceil(log2 W), mul = floor(2^(31+l) / W) + 1, shr = l - 1.  Checked
+    against integer division for every width class the library accepts
+    (multiples of 16, powers of two and not) on edge and random indices."""
+    import numpy as np
+    rng = np.random.default_rng(3)
+    widths = [16, 32, 48, 96, 144, 176, 480, 1008, 1024, 1424, 2048, 4080, 8192, 65536,
+              65552, 1 << 20, (1 << 27) - 16, 1 << 27]
+    for W in widths:
+        l = int(W - 1).bit_length()
+        mul = (1 << (31 + l)) // W + 1
+        shr = l - 1
+        assert mul < (1 << 32)
+        k = np.arange(1, 4096, dtype=np.int64)
+        near = np.arange(min(4 * W, 65536), dtype=np.int64)
+        c = np.concatenate([rng.integers(0, 1 << 31, 200_000, dtype=np.int64), near,
+                            (1 << 31) - 1 - near, k * W - 1, k * W,
+                            ((1 << 31) // W - k) * W, ((1 << 31) // W - k) * W - 1]).astype(np.uint64)
+        c = c[c < (1 << 31)]
+        q = ((c * np.uint64(mul)) >> np.uint64(32)) >> np.uint64(shr)
+        assert np.array_equal(q, c // np.uint64(W)), W
