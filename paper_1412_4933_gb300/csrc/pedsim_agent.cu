@@ -1,13 +1,16 @@
 // Agent-parallel step (PEDSIM_VARIANT_AGENT) of the pedestrian cellular
-// automaton (sm_103a).  One synchronous step (Sec. IV.b-d) is split by
+// automaton (sm_103a), and its deferred-evaporation form
+// (PEDSIM_VARIANT_DEFERRED).  One synchronous step (Sec. IV.b-d) is split by
 // access pattern instead of by tile, in two kernels:
 //
 //   agent_stage1_kernel   two CTA roles, the proposal blocks first:
 //     proposal blocks     one thread per agent: forward first, else the full
 //                         rule (Eq. 1 LEM rank draw, Eq. 2 ACO roulette) from
-//                         the occupancy and pheromone at t; the direction code
-//                         goes to the agent's entry of `acode` and to its own
-//                         cell of the step's code plane
+//                         the occupancy and pheromone at t, the blocked agents
+//                         compacted into full warps; the direction code goes
+//                         to the agent's entry of `acode` and to its own cell
+//                         of the step's code plane, a claimed flag to its
+//                         target's byte
 //     stream blocks       every cell: both pheromone planes evaporated into
 //                         the planes of t+1 (Eq. 3); a pure 16-byte-vector
 //                         stream, the HBM-bound part of the step (ACO only)
@@ -20,8 +23,15 @@
 //                         (Eq. 4/5) on top of the evaporated value; beside the
 //                         agent CTAs, stream CTAs evaporate the step's last
 //                         cell blocks (as many as fill one resident wave),
-//                         skipping the claimed cells (found from the same
-//                         codes), whose winners write both planes
+//                         skipping the claimed cells (from the flags), whose
+//                         winners write both planes
+//
+//   deferred_stage1_kernel / deferred_resolve_kernel
+//                         the same without the stream: one pheromone plane per
+//                         group updated in place and a per-cell stamp; values
+//                         are brought up to date where they are read and in a
+//                         rolling refresh of 1/kDeferPeriod of the cell blocks
+//                         per step (bit-identical to evaporating every cell)
 //
 // Occupancy lives in one plane, occ[0], updated in place: the proposals read
 // it (state at t) in the first kernel, the moves are applied to it only in
