@@ -726,9 +726,13 @@ __device__ __forceinline__ float evaporate_n(float v, uint32_t age, float q)
     return v;
 }
 
-// First kernel of the deferred step: the proposals only (six resident CTAs
-// per SM, as the agent step's first kernel).
-__global__ void __launch_bounds__(kAgentBlock, 6)
+// First kernel of the deferred step: the proposals only.  Two builds: with
+// no register cap (four CTAs per SM) for launches whose proposal CTAs fit one
+// resident wave, where each agent's chain of loads is the step's critical
+// path; and capped at six CTAs per SM for larger launches, which are
+// throughput-bound and gain from the occupancy.
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kAgentBlock, kMinBlocks)
 deferred_stage1_kernel(const ScenarioDesc *__restrict__ descs,
                        const uint32_t *__restrict__ agent_prefix, int n_scen, uint32_t agent_blocks,
                        int prefetch)
@@ -1028,7 +1032,7 @@ static uint32_t resolve_wave()
 static uint32_t deferred_stage1_wave()
 {
     static std::atomic<uint32_t> cache[kMaxDevices];
-    return resident_wave(deferred_stage1_kernel, cache);
+    return resident_wave(deferred_stage1_kernel<6>, cache);
 }
 
 static uint32_t deferred_resolve_wave()
@@ -1094,9 +1098,11 @@ cudaError_t launch_deferred_step(const ScenarioDesc *d_descs, const uint32_t *d_
     // speculative loads only while each kernel's CTAs fit in one resident
     // wave (latency-bound); a launch with more agents is throughput-bound
     const int pre1 = agent_blocks <= deferred_stage1_wave();
-    cudaError_t e = launch_pdl(deferred_stage1_kernel, agent_blocks > 0 ? agent_blocks : 1u,
-                               (unsigned)kAgentBlock, stream, d_descs, d_agent_prefix, n,
-                               agent_blocks, pre1);
+    const unsigned g1 = agent_blocks > 0 ? agent_blocks : 1u;
+    cudaError_t e = pre1 ? launch_pdl(deferred_stage1_kernel<1>, g1, (unsigned)kAgentBlock, stream,
+                                      d_descs, d_agent_prefix, n, agent_blocks, pre1)
+                         : launch_pdl(deferred_stage1_kernel<6>, g1, (unsigned)kAgentBlock, stream,
+                                      d_descs, d_agent_prefix, n, agent_blocks, pre1);
     if (e != cudaSuccess) return e;
     const uint32_t g = agent_blocks + slices > 0 ? agent_blocks + slices : 1u;
     const int pre2 = g <= deferred_resolve_wave();
