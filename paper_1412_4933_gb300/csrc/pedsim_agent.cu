@@ -207,7 +207,16 @@ __device__ __forceinline__ void propose_block(const ScenarioDesc &d, uint32_t lb
     __shared__ BlockedAgent blocked[kAgentBlock];
     __shared__ uint32_t warp_base[kAgentBlock / 32 + 1];
     const uint32_t a = lb * kAgentBlock + threadIdx.x;
-    const bool live = t < d.end_step && a < 2u * d.n_per_side;
+    // the position and per-agent byte are loaded whatever the step index, so
+    // that they share a round of loads with it (the callers read it from L2
+    // after their wait)
+    const bool in = a < 2u * d.n_per_side;
+    uint32_t cell0 = 0, prev0 = 0;
+    if (in) {
+        cell0 = __ldg(d.pos + a + 1u);
+        prev0 = __ldg(d.acode + a + 1u);
+    }
+    const bool live = in && t < d.end_step;
     const int W = d.W, H = d.H;
     const int p = (int)(t & 1);
     bool is_blocked = false;
@@ -217,8 +226,8 @@ __device__ __forceinline__ void propose_block(const ScenarioDesc &d, uint32_t lb
     uint32_t pst[9];
     if (live) {
         id = a + 1u;
-        cell = __ldg(d.pos + id);
-        const int prev = __ldg(d.acode + id);
+        cell = cell0;
+        const int prev = (int)prev0;
         g = prev >> 4 & 3;
         const uint32_t yr = cell_row(d, cell);
         const int x = (int)(cell - yr * (uint32_t)W), y = (int)yr;
@@ -355,10 +364,7 @@ agent_stage1_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__re
                     const uint32_t *__restrict__ agent_prefix, int n_scen, uint32_t cell_blocks,
                     uint32_t agent_blocks, uint32_t front, int prefetch)
 {
-    // The state at t is the previous step's output: wait for it, then let
-    // the resolution kernel be scheduled (it waits for this one).
-    pdl_wait();
-    pdl_trigger();
+    __shared__ __align__(128) ScenarioDesc hdr;  // header part only (proposal CTAs)
     // (cell_blocks here counts the blocks this kernel streams: the first
     // ones; the resolution kernel evaporates the rest)
     // CTAs 0 .. front-1 are the first proposal blocks (at most one resident
@@ -392,12 +398,24 @@ agent_stage1_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__re
             }
         }
     }
+    // The state at t is the previous step's output: each CTA waits for it,
+    // then lets the resolution kernel be scheduled (it waits for this one).
     if (b >= agent_blocks) {
+        pdl_wait();
+        pdl_trigger();
         stream_block(descs, cell_prefix, n_scen, sb);
     } else {
+        // A proposal CTA copies its scenario's descriptor header (constant
+        // during the step but for the step index) before the wait; after
+        // it, the step index (from L2: the previous step's resolution
+        // advanced it) is read in one round with the agents' positions.
         const int s = block_scenario(agent_prefix, n_scen, b);
-        const ScenarioDesc &d = descs[s];
-        propose_block<false>(d, b - __ldg(agent_prefix + s), d.step, prefetch != 0);
+        const uint32_t lb = b - __ldg(agent_prefix + s);
+        load_header(&hdr, descs + s);
+        pdl_wait();
+        pdl_trigger();
+        __syncthreads();
+        propose_block<false>(hdr, lb, __ldcg(&descs[s].step), prefetch != 0);
     }
 }
 
@@ -737,13 +755,22 @@ deferred_stage1_kernel(const ScenarioDesc *__restrict__ descs,
                        const uint32_t *__restrict__ agent_prefix, int n_scen, uint32_t agent_blocks,
                        int prefetch)
 {
+    __shared__ __align__(128) ScenarioDesc hdr;  // header part only
+    const uint32_t b = blockIdx.x;
+    if (b >= agent_blocks) {
+        pdl_wait();
+        pdl_trigger();
+        return;
+    }
+    // the descriptor header before the wait, the step index after it (see
+    // agent_stage1_kernel)
+    const int s = block_scenario(agent_prefix, n_scen, b);
+    const uint32_t lb = b - __ldg(agent_prefix + s);
+    load_header(&hdr, descs + s);
     pdl_wait();
     pdl_trigger();
-    const uint32_t b = blockIdx.x;
-    if (b >= agent_blocks) return;
-    const int s = block_scenario(agent_prefix, n_scen, b);
-    const ScenarioDesc &d = descs[s];
-    propose_block<true>(d, b - __ldg(agent_prefix + s), d.step, prefetch != 0);
+    __syncthreads();
+    propose_block<true>(hdr, lb, __ldcg(&descs[s].step), prefetch != 0);
 }
 
 // Rolling refresh of cell block b of scenario d at step t: every unclaimed

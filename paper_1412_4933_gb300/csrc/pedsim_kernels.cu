@@ -1022,15 +1022,6 @@ __device__ __forceinline__ bool cta_wait_tma(uint64_t *bar, uint32_t parity,
     return __syncthreads_and(ok);
 }
 
-// Copies a scenario's descriptor header into shared memory (16 bytes per
-// thread of the first 16 threads); the caller synchronises.
-__device__ __forceinline__ void load_header(ScenarioDesc *dst, const ScenarioDesc *src)
-{
-    if (threadIdx.x < kDescHeaderBytes / 16)
-        reinterpret_cast<uint4 *>(dst)[threadIdx.x] =
-            __ldg(reinterpret_cast<const uint4 *>(src) + threadIdx.x);
-}
-
 template <int TH>
 __global__ void __launch_bounds__(8 * TH)
 propose_tile_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__restrict__ tile_prefix,

@@ -112,6 +112,17 @@ __device__ __forceinline__ void fence_mbarrier_init()
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Copies a scenario's descriptor header into shared memory (16 bytes per
+// thread of the first kDescHeaderBytes / 16 threads); the caller
+// synchronises.  The copy goes through the read-only path, so only fields
+// that no kernel writes may be read from it (not the step index).
+__device__ __forceinline__ void load_header(ScenarioDesc *dst, const ScenarioDesc *src)
+{
+    if (threadIdx.x < kDescHeaderBytes / 16)
+        reinterpret_cast<uint4 *>(dst)[threadIdx.x] =
+            __ldg(reinterpret_cast<const uint4 *>(src) + threadIdx.x);
+}
+
 // Per-thread step counters (moved, conflicts, crossings per group).
 struct Counts {
     unsigned moved = 0, conflicts = 0, crossed_a = 0, crossed_b = 0;
