@@ -548,16 +548,20 @@ def deferred_leg(P, torch, sc, stream, warmup: int, steps: int, repeats: int, he
             "device_status": status}
 
 
-def serving_leg(P, torch, stream, n_requests=200, budget_frac=0.5, chunk=16):
-    """Poisson request stream (200/s) through the continuous-batching loop."""
+def serving_leg(P, torch, stream, n_requests=200, budget_frac=0.5, chunk=16, warmup=4):
+    """Poisson request stream (200/s) through the continuous-batching loop,
+    after `warmup` requests of another stream served untimed on the same
+    loop (the pool's memory and graphs exist before the timed stream)."""
     from paper_1412_4933_gb300 import serving
     reqs = WL.serving_requests(n_requests)
     free, _ = torch.cuda.mem_get_info()
     loop = serving.ServingLoop(int(free * budget_frac), 512, chunk=chunk, stream=stream)
+    loop.run(WL.serving_requests(warmup, arrival_seed=8), realtime=False)
     rep = loop.run(reqs)
     loop.close()
     out = rep.summary()
-    out.update({"rate_per_s": 200.0, "hbm_budget_frac": budget_frac, "chunk_steps": chunk})
+    out.update({"rate_per_s": 200.0, "hbm_budget_frac": budget_frac, "chunk_steps": chunk,
+                "warmup_requests": warmup})
     return out
 
 

@@ -280,7 +280,10 @@ const char *sim_batch_last_error(const batch_t *b);
 typedef struct pool_s pool_t;
 
 /* hbm_budget_bytes bounds the sum of sim_device_bytes() of live slots;
- * max_slots bounds their number.                                              */
+ * max_slots bounds their number.  The slots are allocated from a CUDA memory
+ * pool of the pool's own on the current device, which keeps up to
+ * hbm_budget_bytes reserved while slots come and go (released to the system
+ * by sim_pool_destroy).  PEDSIM_ECUDA if that pool cannot be created.         */
 int sim_pool_create(size_t hbm_budget_bytes, int max_slots, pool_t **out);
 int sim_pool_set_stream(pool_t *pl, void *stream);
 /* Admits one request: allocates its state, places it with `seed` and

@@ -468,8 +468,10 @@ int switch_variant(sim_t *s, int variant, int tw, int th, int cps)
 
 // Creates a scenario whose allocation, initialisation and later work are
 // ordered on `stream` (stream-ordered allocation: no device-wide sync).
+// `mem`: the memory pool the allocation comes from (nullptr: the device's
+// default pool).
 static int pedsim_create_on_stream(int W, int H, const sim_params *p, cudaStream_t stream,
-                                   sim_t **out)
+                                   sim_t **out, cudaMemPool_t mem = nullptr)
 {
     if (!out) return PEDSIM_EINVAL;
     *out = nullptr;
@@ -482,7 +484,9 @@ static int pedsim_create_on_stream(int W, int H, const sim_params *p, cudaStream
     s->stream = stream;
     s->L = make_layout(W, H, *p);
     s->sms = device_sms();
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&s->dmem), s->L.total, stream);
+    cudaError_t e =
+        mem ? cudaMallocFromPoolAsync(reinterpret_cast<void **>(&s->dmem), s->L.total, mem, stream)
+            : cudaMallocAsync(reinterpret_cast<void **>(&s->dmem), s->L.total, stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete s;
@@ -1077,6 +1081,11 @@ struct batch_s {
 struct pool_s {
     size_t budget = 0, in_use = 0;
     int max_slots = 0;
+    // The slots' memory pool: it keeps up to the budget reserved when slots
+    // are released (the device's default pool returns freed memory to the
+    // system at the next synchronisation, so each admission would map its
+    // pages again).
+    cudaMemPool_t mem = nullptr;
     std::vector<sim_t *> slots;        // nullptr = free
     std::vector<size_t> bytes;
     bool dirty = true;
@@ -1223,6 +1232,21 @@ int sim_pool_create(size_t hbm_budget_bytes, int max_slots, pool_t **out)
         delete pl;
         return PEDSIM_ECUDA;
     }
+    int dev = 0;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    const unsigned long long keep = hbm_budget_bytes;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        (props.location.id = dev, cudaMemPoolCreate(&pl->mem, &props)) != cudaSuccess ||
+        cudaMemPoolSetAttribute(pl->mem, cudaMemPoolAttrReleaseThreshold,
+                                const_cast<unsigned long long *>(&keep)) != cudaSuccess) {
+        cudaGetLastError();
+        if (pl->mem) cudaMemPoolDestroy(pl->mem);
+        cudaStreamDestroy(pl->run.cap);
+        delete pl;
+        return PEDSIM_ECUDA;
+    }
     *out = pl;
     return PEDSIM_OK;
 }
@@ -1249,7 +1273,7 @@ int sim_pool_admit(pool_t *pl, int W, int H, const sim_params *p, uint64_t seed,
         return PEDSIM_ENOSPC;
     }
     sim_t *s = nullptr;
-    int rc = pedsim_create_on_stream(W, H, p, pl->run.stream, &s);
+    int rc = pedsim_create_on_stream(W, H, p, pl->run.stream, &s, pl->mem);
     if (rc) { pl->run.err = "slot creation failed"; return rc; }
     s->end_step = steps;
     rc = retile(s, pl->run.variant, pl->run.tile_w, pl->run.tile_h, pl->run.ctas_per_sm);
@@ -1359,6 +1383,9 @@ void sim_pool_destroy(pool_t *pl)
     pl->run.release();
     for (sim_t *s : pl->slots)
         if (s) sim_destroy(s);
+    // (the pool's memory is given back once the slots' stream-ordered frees
+    // have run)
+    if (pl->mem) cudaMemPoolDestroy(pl->mem);
     delete pl;
 }
 
