@@ -264,18 +264,23 @@ __device__ __forceinline__ void propose_block(const ScenarioDesc &d, uint32_t lb
             d.acode[id] = (uint8_t)(code | (g << 4));
         }
     }
-    // compaction of the blocked agents
+    // compaction of the blocked agents: each warp's count, then every thread
+    // sums the counts of the warps before its own (its warp's offset) and of
+    // all warps (the list's length) -- independent shared-memory reads
+    // instead of a serial scan and a second barrier
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const unsigned ballot = __ballot_sync(0xffffffffu, is_blocked);
-    if (lane == 0) warp_base[warp + 1] = (uint32_t)__popc(ballot);
+    if (lane == 0) warp_base[warp] = (uint32_t)__popc(ballot);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        warp_base[0] = 0;
-        for (int w = 1; w <= kAgentBlock / 32; ++w) warp_base[w] += warp_base[w - 1];
+    uint32_t base = 0, nb = 0;
+#pragma unroll
+    for (unsigned w = 0; w < kAgentBlock / 32; ++w) {
+        const uint32_t c = warp_base[w];
+        base += w < warp ? c : 0u;
+        nb += c;
     }
-    __syncthreads();
     if (is_blocked) {
-        BlockedAgent &e = blocked[warp_base[warp] + __popc(ballot & ((1u << lane) - 1u))];
+        BlockedAgent &e = blocked[base + __popc(ballot & ((1u << lane) - 1u))];
         if (d.tau[0][0] && prefetch) {
 #pragma unroll
             for (int i = 1; i <= 8; ++i) {
@@ -289,7 +294,6 @@ __device__ __forceinline__ void propose_block(const ScenarioDesc &d, uint32_t lb
         e.g = (uint32_t)g;
     }
     __syncthreads();
-    const uint32_t nb = warp_base[kAgentBlock / 32];
     if (threadIdx.x < nb) {
         const BlockedAgent &e = blocked[threadIdx.x];
         const RuleParams rp{d.model, d.alpha, d.beta, d.lem_scale};
@@ -677,6 +681,14 @@ agent_resolve_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__r
         live[q] = tq[q] < dq[q]->end_step && a < 2u * dq[q]->n_per_side;
         if (live[q]) resolve_load_own(*dq[q], a, r[q]);
     }
+    // Every thread of the CTA has read its step index: the CTA takes its
+    // ticket now, before the wait (the reply is needed only at the end).  The
+    // CTA holding the last ticket advances the step index of every scenario
+    // of the work list (clamped at its end) after its own work: by then
+    // every CTA has read it.
+    __syncthreads();
+    unsigned int ticket = 0;
+    if (threadIdx.x == 0) ticket = atomicAdd(&ctl->ticket, 1u);
     pdl_wait();  // first kernel (proposals and stream) complete
     pdl_trigger();
 #pragma unroll
@@ -684,13 +696,6 @@ agent_resolve_kernel(const ScenarioDesc *__restrict__ descs, const uint32_t *__r
         if (live[q]) resolve_load_code(*dq[q], r[q]);
         if (live[q] && r[q].code == 0) live[q] = false;
     }
-    // Every thread of the CTA has read its step index: the CTA takes its
-    // ticket now (the reply is needed only at the end).  The CTA holding the
-    // last ticket advances the step index of every scenario of the work list
-    // (clamped at its end) after its own work: by then every CTA has read it.
-    __syncthreads();
-    unsigned int ticket = 0;
-    if (threadIdx.x == 0) ticket = atomicAdd(&ctl->ticket, 1u);
 #pragma unroll
     for (int q = 0; q < kResolveBlocks; ++q)
         if (live[q]) resolve_load_target(*dq[q], tq[q], r[q], late_from[q]);
@@ -901,14 +906,14 @@ deferred_resolve_kernel(const ScenarioDesc *__restrict__ descs,
                 st[j] = ok ? ld_nc_u8(d.stamp + off) : 0u;
             }
         }
+        __syncthreads();  // every thread has read the step index: the ticket
+        if (threadIdx.x == 0) ticket = atomicAdd(&ctl->ticket, 1u);
         pdl_wait();  // proposals complete
         pdl_trigger();
         if (live) {
             resolve_load_code(d, r);
             live = r.code != 0;
         }
-        __syncthreads();  // every thread has read the step index
-        if (threadIdx.x == 0) ticket = atomicAdd(&ctl->ticket, 1u);
         Counts cnt;
         if (live) {
             // the target's claimants from its neighbours' codes
