@@ -40,7 +40,7 @@ Also reported on the same line:
                 simulation's own L2-resident regime
   inputs_larger_than_l2
                 four independent copies of the headline scenario advanced
-                together (inputs 4 x 101 MiB > L2), graph replays timed with
+                together (inputs 4 x 105 MiB > L2), graph replays timed with
                 one event pair: the cold-L2 step without per-step events
   batched       256 uneven scenarios x 500 steps in batched launches (the
                 autotuner's configuration), vs the same scenarios and steps
@@ -72,7 +72,7 @@ sys.path.insert(0, ROOT)
 from paper_1412_4933_gb300 import workloads as WL  # noqa: E402
 
 L2_FLUSH_BYTES = 512 << 20
-ROTATING_INSTANCES = 4  # headline: 4 x 101 MiB of state at 2048^2, well above the L2
+ROTATING_INSTANCES = 4  # headline: 4 x 105 MiB of state at 2048^2, well above the L2
 NOMINAL_HBM_GBPS = 7900.0  # GB300 HBM3e nominal, for context beside the measured peak
 ALGO_BYTES_PER_CELL = {WL.LEM: 2, WL.ACO: 18}
 KERNEL_SOURCES = ["paper_1412_4933_gb300/csrc/pedsim_agent.cu",
@@ -408,7 +408,7 @@ def e2e_run(P, torch, sc, stream, reps: int):
 
 def large_inputs_leg(P, torch, sc, stream, instances=4, steps=96):
     """The headline scenario with inputs larger than L2 instead of a flush:
-    `instances` independent copies (seeds sc.seed + k; 4 x 101 MiB > 129 MB
+    `instances` independent copies (seeds sc.seed + k; 4 x 105 MiB > 129 MB
     L2) advanced together as a batch, so every step streams its planes from
     HBM; graph replays timed with one event pair (no per-step events)."""
     scs = [sc.with_(seed=sc.seed + k, name=f"{sc.name}#{k}") for k in range(instances)]
