@@ -843,7 +843,11 @@ __device__ __forceinline__ void refresh_block(const ScenarioDesc &d, uint64_t t,
 // stamp t + 1.  The CTAs after them refresh the step's slice of cell blocks:
 // CTA j of scenario s (slice_prefix) takes block j * kDeferPeriod + t mod
 // kDeferPeriod.  The CTA holding the last ticket advances the step indices.
-__global__ void __launch_bounds__(kAgentBlock, 5)
+// Two builds: four CTAs per SM (64 registers, no spills of the prefetched
+// values) for launches that fit one resident wave of that build, five CTAs
+// per SM (48 registers) for larger ones.
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kAgentBlock, kMinBlocks)
 deferred_resolve_kernel(const ScenarioDesc *__restrict__ descs,
                         const uint32_t *__restrict__ agent_prefix,
                         const uint32_t *__restrict__ cell_prefix,
@@ -1070,7 +1074,13 @@ static uint32_t deferred_stage1_wave()
 static uint32_t deferred_resolve_wave()
 {
     static std::atomic<uint32_t> cache[kMaxDevices];
-    return resident_wave(deferred_resolve_kernel, cache);
+    return resident_wave(deferred_resolve_kernel<5>, cache);
+}
+
+static uint32_t deferred_resolve_wave4()
+{
+    static std::atomic<uint32_t> cache[kMaxDevices];
+    return resident_wave(deferred_resolve_kernel<4>, cache);
 }
 
 // Cell blocks of a step evaporated in the resolution kernel: the free part
@@ -1137,8 +1147,11 @@ cudaError_t launch_deferred_step(const ScenarioDesc *d_descs, const uint32_t *d_
                                       d_descs, d_agent_prefix, n, agent_blocks, pre1);
     if (e != cudaSuccess) return e;
     const uint32_t g = agent_blocks + slices > 0 ? agent_blocks + slices : 1u;
+    if (g <= deferred_resolve_wave4())
+        return launch_pdl(deferred_resolve_kernel<4>, g, (unsigned)kAgentBlock, stream, d_descs,
+                          d_agent_prefix, d_cell_prefix, d_slice_prefix, n, agent_blocks, ctl, 1);
     const int pre2 = g <= deferred_resolve_wave();
-    return launch_pdl(deferred_resolve_kernel, g, (unsigned)kAgentBlock, stream, d_descs,
+    return launch_pdl(deferred_resolve_kernel<5>, g, (unsigned)kAgentBlock, stream, d_descs,
                       d_agent_prefix, d_cell_prefix, d_slice_prefix, n, agent_blocks, ctl, pre2);
 }
 
@@ -1162,6 +1175,7 @@ cudaError_t launch_build_pos(const ScenarioDesc *d_desc, int cells, int plane, c
     (void)resolve_wave();
     (void)deferred_stage1_wave();
     (void)deferred_resolve_wave();
+    (void)deferred_resolve_wave4();
     int blocks = (cells + 255) / 256;
     if (blocks > 1024) blocks = 1024;
     if (blocks < 1) blocks = 1;
