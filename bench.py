@@ -46,6 +46,9 @@ Also reported on the same line:
                 autotuner's configuration), vs the same scenarios and steps
                 run one scenario at a time; algorithmic GB/s beside it
   serving       Poisson request stream through the serving pool: p50/p99
+  domain_strips the headline workload as two column strips on this GPU
+                (per-strip step plus halo exchange between the strips),
+                beside the single-grid step
 
 `--impl reference` times the CPU oracle instead (the reference arm).
 Under torchrun each rank runs an independent replica (no collective on the
@@ -548,6 +551,40 @@ def deferred_leg(P, torch, sc, stream, warmup: int, steps: int, repeats: int, he
             "device_status": status}
 
 
+def domain_leg(P, torch, sc, stream, warmup: int, steps: int, headline_s: float, n_strips=2):
+    """The headline workload advanced as `n_strips` column strips on this one
+    GPU (``sim_step_strip`` per strip; before every step each strip's three
+    halo columns are refreshed from its neighbours' interiors), from the
+    state a placed scenario reaches after `warmup` steps.  Here the halo
+    exchange is one ``sim_strip_halo`` kernel per halo between the strips'
+    tensors on one device; between GPUs it is point-to-point sends
+    (domain.DistExchange), which one GPU cannot time."""
+    from paper_1412_4933_gb300 import domain as D
+    sim = P.Sim(sc.W, sc.H, P.params_of(sc), stream=stream)
+    with torch.cuda.stream(stream):
+        sim.place(sc.seed)
+        sim.step(warmup)
+    grid, agents = sim.read_grid(), sim.read_agents()
+    sim.close()
+    dom = D.StripDomain(sc.W, sc.H, P.params_of(sc), sc.seed, n_strips)
+    with torch.cuda.stream(stream):
+        dom.load(warmup, grid, agents)
+        dom.step(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dom.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    step_s = e0.elapsed_time(e1) * 1e-3 / steps
+    return {"strips": n_strips, "steps": steps, "us_per_step": step_s * 1e6,
+            "cell_updates_per_s": sc.cells / step_s,
+            "single_grid_us_per_step": headline_s * 1e6,
+            "exchange": "one sim_strip_halo kernel per halo between the strips' tensors "
+                        "on one GPU; per step two halo copies and two sim_step_strip calls "
+                        "issued from Python"}
+
+
 def serving_leg(P, torch, stream, n_requests=200, budget_frac=0.5, chunk=16, warmup=4):
     """Poisson request stream (200/s) through the continuous-batching loop,
     after `warmup` requests of another stream served untimed on the same
@@ -668,6 +705,9 @@ def run_gpu(args, sc):
         extra["inputs_larger_than_l2"] = large_inputs_leg(P, torch, sc, stream)
     if rank == 0 and not args.quick and not args.no_batched:
         extra["batched"] = batched_leg(P, torch, stream)
+    if rank == 0 and not args.quick and not args.no_domain:
+        extra["domain_strips"] = domain_leg(P, torch, sc, stream, args.warmup, args.steps,
+                                            elapsed_max / args.steps)
     if rank == 0 and not args.quick and not args.no_serving:
         extra["serving"] = serving_leg(P, torch, stream)
 
@@ -726,6 +766,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-domain", action="store_true",
+                    help="skip the column-strip decomposition leg")
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--quick", action="store_true", help="headline only (for profiling runs)")
     args = ap.parse_args()

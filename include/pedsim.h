@@ -348,6 +348,26 @@ int sim_step_strip(int W, int H, int x0, int W_global, int interior_lo, int inte
                    float *tauA_out, float *tauB_out, uint32_t *arrival, float *tour,
                    uint8_t *scratch, unsigned long long *counters, void *stream);
 
+/* Halo exchange between two strips on one device (or on devices with peer
+ * access): columns [src_col, src_col + ncols) of the source strip's local
+ * planes (width src_W) are copied into columns [dst_col, dst_col + ncols) of
+ * the destination's (width dst_W), both H rows -- occupancy, ids and, for
+ * ACO, both pheromone planes of the step's parity -- and for every copied
+ * cell holding agent id (1..n_agents) that agent's arrival step and tour
+ * length are copied from the source's per-agent arrays into the
+ * destination's (n_agents + 1 entries each; the tour pair may be NULL when
+ * the scenario keeps none).  This is the exchange sim_step_strip expects
+ * between steps.  All pointers are device memory of the caller; the tau
+ * pointers are all NULL (LEM) or all set.  Asynchronous on `stream` (NULL =
+ * the legacy default stream), one kernel, no allocation; PEDSIM_EINVAL for
+ * columns outside either strip or inconsistent NULL pointers, PEDSIM_ECUDA
+ * when the launch fails.                                                      */
+int sim_strip_halo(int H, int ncols, uint32_t n_agents, const uint8_t *src_occ,
+                   const uint32_t *src_ids, const float *src_tauA, const float *src_tauB,
+                   const uint32_t *src_arrival, const float *src_tour, int src_W, int src_col,
+                   uint8_t *dst_occ, uint32_t *dst_ids, float *dst_tauA, float *dst_tauB,
+                   uint32_t *dst_arrival, float *dst_tour, int dst_W, int dst_col, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Allocation-free step.  The paper has no counterpart: this entry point     */
 /* exists for callers that cannot let a library allocate device memory while */

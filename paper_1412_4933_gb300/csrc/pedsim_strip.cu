@@ -161,10 +161,95 @@ bool shares_bytes(const void *a, const void *b, size_t n)
     return x < y + n && y < x + n;
 }
 
+// Halo copy between two strips: columns [src_col, src_col + ncols) of the
+// source's local planes into [dst_col, ...) of the destination's, and the
+// per-agent entries of the agents standing on the copied cells.
+struct HaloCopy {
+    int H, ncols, src_W, src_col, dst_W, dst_col;
+    uint32_t n_agents;  // per-agent arrays hold n_agents + 1 entries
+    const uint8_t *src_occ;
+    const uint32_t *src_ids;
+    const float *src_tau[2];
+    const uint32_t *src_arrival;
+    const float *src_tour;
+    uint8_t *dst_occ;
+    uint32_t *dst_ids;
+    float *dst_tau[2];
+    uint32_t *dst_arrival;
+    float *dst_tour;
+};
+
+__global__ void __launch_bounds__(kStripThreads) strip_halo_kernel(const HaloCopy a)
+{
+    const size_t n = (size_t)a.H * (size_t)a.ncols;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const size_t y = i / (size_t)a.ncols, c = i - y * (size_t)a.ncols;
+        const size_t s = y * (size_t)a.src_W + (size_t)a.src_col + c;
+        const size_t d = y * (size_t)a.dst_W + (size_t)a.dst_col + c;
+        const uint8_t o = a.src_occ[s];
+        const uint32_t id = a.src_ids[s];
+        a.dst_occ[d] = o;
+        a.dst_ids[d] = id;
+        if (a.src_tau[0]) {
+            a.dst_tau[0][d] = a.src_tau[0][s];
+            a.dst_tau[1][d] = a.src_tau[1][s];
+        }
+        if (o && id >= 1u && id <= a.n_agents) {
+            a.dst_arrival[id] = a.src_arrival[id];
+            if (a.src_tour) a.dst_tour[id] = a.src_tour[id];
+        }
+    }
+}
+
 }  // namespace
 }  // namespace pedsim
 
 using namespace pedsim;
+
+extern "C" int sim_strip_halo(int H, int ncols, uint32_t n_agents, const uint8_t *src_occ,
+                              const uint32_t *src_ids, const float *src_tauA,
+                              const float *src_tauB, const uint32_t *src_arrival,
+                              const float *src_tour, int src_W, int src_col, uint8_t *dst_occ,
+                              uint32_t *dst_ids, float *dst_tauA, float *dst_tauB,
+                              uint32_t *dst_arrival, float *dst_tour, int dst_W, int dst_col,
+                              void *stream)
+{
+    if (H < 1 || ncols < 0 || src_W < 1 || dst_W < 1 || src_col < 0 || dst_col < 0 ||
+        src_col + ncols > src_W || dst_col + ncols > dst_W)
+        return PEDSIM_EINVAL;
+    if (!src_occ || !src_ids || !src_arrival || !dst_occ || !dst_ids || !dst_arrival)
+        return PEDSIM_EINVAL;
+    if (!src_tauA != !src_tauB || !src_tauA != !dst_tauA || !dst_tauA != !dst_tauB)
+        return PEDSIM_EINVAL;
+    if (!src_tour != !dst_tour) return PEDSIM_EINVAL;
+    if (ncols == 0) return PEDSIM_OK;
+    HaloCopy a{};
+    a.H = H;
+    a.ncols = ncols;
+    a.src_W = src_W;
+    a.src_col = src_col;
+    a.dst_W = dst_W;
+    a.dst_col = dst_col;
+    a.n_agents = n_agents;
+    a.src_occ = src_occ;
+    a.src_ids = src_ids;
+    a.src_tau[0] = src_tauA;
+    a.src_tau[1] = src_tauB;
+    a.src_arrival = src_arrival;
+    a.src_tour = src_tour;
+    a.dst_occ = dst_occ;
+    a.dst_ids = dst_ids;
+    a.dst_tau[0] = dst_tauA;
+    a.dst_tau[1] = dst_tauB;
+    a.dst_arrival = dst_arrival;
+    a.dst_tour = dst_tour;
+    const size_t n = (size_t)H * (size_t)ncols;
+    size_t blocks = (n + kStripThreads - 1) / kStripThreads;
+    if (blocks > 1024) blocks = 1024;
+    strip_halo_kernel<<<(unsigned)blocks, kStripThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError() == cudaSuccess ? PEDSIM_OK : PEDSIM_ECUDA;
+}
 
 extern "C" int sim_step_strip(int W, int H, int x0, int W_global, int interior_lo,
                               int interior_hi, const sim_params *p, uint64_t seed, uint64_t step,

@@ -124,22 +124,42 @@ def apply_slab(st: StripState, par: int, g0: int, g1: int, packed) -> None:
 
 
 class LocalExchange:
-    """Halo exchange between strips held by this process."""
+    """Halo exchange between strips held by this process: between strips on
+    the same GPU one ``sim_strip_halo`` kernel per halo (the library's copy of
+    the planes and of the halo agents' entries, no host synchronisation),
+    otherwise the packed slabs through torch."""
 
     def __init__(self, strips):
         self.strips = strips
+
+    @staticmethod
+    def _copy(src: StripState, dst: StripState, par: int, g0: int, g1: int) -> None:
+        if not (src.ids.is_cuda and src.ids.device == dst.ids.device):
+            apply_slab(dst, par, g0, g1, [t.to(dst.ids.device) for t in slab(src, par, g0, g1)])
+            return
+        import torch
+        from . import pedsim as P
+
+        def bufs(st):
+            tau = (st.tau[0][par], st.tau[1][par]) if st.tau is not None else (None, None)
+            return (st.occ[par], st.ids) + tau + (st.arrival, st.tour)
+
+        rc = P.strip_halo(dst.occ[par].shape[0], g1 - g0, dst.arrival.numel() - 1,
+                          bufs(src), src.layout.width, src.layout.local(g0, g1).start,
+                          bufs(dst), dst.layout.width, dst.layout.local(g0, g1).start,
+                          stream=torch.cuda.current_stream(dst.ids.device))
+        if rc != P.OK:
+            raise P.PedsimError(rc, "sim_strip_halo failed")
 
     def exchange(self, par: int) -> None:
         for r, st in enumerate(self.strips):
             lay = st.layout
             if r > 0 and lay.ea < lay.a:
                 g0, g1 = lay.left_halo()
-                apply_slab(st, par, g0, g1, [t.to(st.ids.device) for t in
-                                             slab(self.strips[r - 1], par, g0, g1)])
+                self._copy(self.strips[r - 1], st, par, g0, g1)
             if r + 1 < len(self.strips) and lay.b < lay.eb:
                 g0, g1 = lay.right_halo()
-                apply_slab(st, par, g0, g1, [t.to(st.ids.device) for t in
-                                             slab(self.strips[r + 1], par, g0, g1)])
+                self._copy(self.strips[r + 1], st, par, g0, g1)
 
 
 class DistExchange:

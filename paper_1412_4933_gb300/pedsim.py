@@ -96,6 +96,8 @@ _SIGS = {
     "sim_step_strip": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                  C.POINTER(SimParams), C.c_uint64, C.c_uint64,
                                  _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "sim_strip_halo": (C.c_int, [C.c_int, C.c_int, C.c_uint32, _P, _P, _P, _P, _P, _P,
+                                 C.c_int, C.c_int, _P, _P, _P, _P, _P, _P, C.c_int, C.c_int, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -421,6 +423,21 @@ def step_strip(W, H, x0, W_global, interior_lo, interior_hi, params: SimParams, 
                                    seed, step, ptr(occ_in), ptr(occ_out), ptr(ids), ptr(tauA_in),
                                    ptr(tauB_in), ptr(tauA_out), ptr(tauB_out), ptr(arrival),
                                    ptr(tour), ptr(scratch), ptr(counters), stream))
+
+
+def strip_halo(H, ncols, n_agents, src, src_W, src_col, dst, dst_W, dst_col,
+               stream=None) -> int:
+    """Halo copy between two strips on one device (``sim_strip_halo``):
+    `src` and `dst` are (occ, ids, tauA, tauB, arrival, tour) device
+    tensors (tauA/tauB None for LEM, tour None when neither keeps one);
+    returns the C status code."""
+    ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+    if stream is None:
+        stream = _default_stream()
+    elif not isinstance(stream, C.c_void_p):
+        stream = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    return int(_lib.sim_strip_halo(H, ncols, n_agents, *(ptr(t) for t in src), src_W, src_col,
+                                   *(ptr(t) for t in dst), dst_W, dst_col, stream))
 
 
 def exported_symbols():

@@ -115,3 +115,29 @@ def test_division_by_width_multiplier():
         c = c[c < (1 << 31)]
         q = ((c * np.uint64(mul)) >> np.uint64(32)) >> np.uint64(shr)
         assert np.array_equal(q, c // np.uint64(W)), W
+
+
+def test_strip_halo_rejects_bad_arguments_before_any_launch(lib_path):
+    """sim_strip_halo validates its columns and pointers on the host: every
+    call here fails before a kernel could start (the pointers are never
+    dereferenced)."""
+    from paper_1412_4933_gb300 import pedsim as P
+    f = P._lib.sim_strip_halo
+    v = C.c_void_p(256)  # stand-in device pointer, never touched
+    none = None
+
+    def call(H=8, ncols=3, src_W=10, src_col=7, dst_W=10, dst_col=0,
+             src_tau=(v, v), dst_tau=(v, v), src_tour=v, dst_tour=v, src_occ=v):
+        return f(H, ncols, 10, src_occ, v, src_tau[0], src_tau[1], v, src_tour, src_W, src_col,
+                 v, v, dst_tau[0], dst_tau[1], v, dst_tour, dst_W, dst_col, none)
+
+    assert call(src_col=8) == P.EINVAL          # source columns past its width
+    assert call(dst_col=8) == P.EINVAL          # destination columns past its width
+    assert call(src_col=-1) == P.EINVAL
+    assert call(H=0) == P.EINVAL
+    assert call(ncols=-1) == P.EINVAL
+    assert call(src_occ=none) == P.EINVAL       # required plane missing
+    assert call(src_tau=(v, none)) == P.EINVAL  # pheromone pointers all or none
+    assert call(dst_tau=(none, none)) == P.EINVAL
+    assert call(dst_tour=none) == P.EINVAL      # tour pointers both or neither
+    assert call(ncols=0) == P.OK                # nothing to copy: no launch
