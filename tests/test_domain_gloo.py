@@ -108,3 +108,48 @@ def test_halo_exchange_with_gloo(world):
         assert ok_planes, f"rank {rank}: halo planes differ from the whole grid"
         assert ok_agents, f"rank {rank}: per-agent entries of halo agents differ"
         assert halo_agents > 0, rank
+
+
+@pytest.mark.parametrize("n_strips", [2, 3])
+def test_local_exchange_on_cpu(n_strips):
+    """LocalExchange between strips held by one process (CPU tensors: the
+    packed-slab path, used between devices): after one exchange every
+    strip's local columns and the entries of every agent on them equal the
+    whole grid's; agents elsewhere keep their (stale) entries."""
+    W, H, n = 48, 20, 150
+    occ, ids, tau, arrival, tour = global_state(W, H, n, 9)
+    layouts = [D.StripLayout(W, a, b) for a, b in D.partition(W, n_strips)]
+    strips = []
+    for lay in layouts:
+        st = D.StripState(torch, lay, H, 2 * n, True, "cpu")
+        st.occ[0].fill_(0)
+        st.ids.fill_(0)
+        for t in (st.tau[0][0], st.tau[1][0]):
+            t.fill_(-1.0)
+        inner = slice(lay.lo, lay.hi)
+        st.occ[0][:, inner] = torch.from_numpy(occ[:, lay.a:lay.b].copy())
+        st.ids[:, inner] = torch.from_numpy(ids[:, lay.a:lay.b].copy())
+        st.tau[0][0][:, inner] = torch.from_numpy(tau[0][:, lay.a:lay.b].copy())
+        st.tau[1][0][:, inner] = torch.from_numpy(tau[1][:, lay.a:lay.b].copy())
+        mine = ids[:, lay.a:lay.b][occ[:, lay.a:lay.b] != 0].astype(np.int64)
+        st.arrival.fill_(-7)
+        st.tour.fill_(-7.0)
+        st.arrival[torch.from_numpy(mine)] = torch.from_numpy(arrival[mine])
+        st.tour[torch.from_numpy(mine)] = torch.from_numpy(tour[mine])
+        strips.append(st)
+    D.LocalExchange(strips).exchange(0)
+    halo_agents = 0
+    for lay, st in zip(layouts, strips):
+        cols = slice(lay.ea, lay.eb)
+        assert np.array_equal(st.occ[0].numpy(), occ[:, cols])
+        on = occ[:, cols] != 0
+        assert np.array_equal(st.ids.numpy()[on], ids[:, cols][on])
+        assert np.array_equal(st.tau[0][0].numpy(), tau[0][:, cols])
+        assert np.array_equal(st.tau[1][0].numpy(), tau[1][:, cols])
+        local = ids[:, cols][on]
+        assert np.array_equal(st.arrival.numpy()[local], arrival[local])
+        assert np.array_equal(st.tour.numpy()[local], tour[local])
+        others = np.setdiff1d(np.arange(1, 2 * n + 1), local)
+        assert (st.arrival.numpy()[others] == -7).all()
+        halo_agents += len(local) - int((occ[:, lay.a:lay.b] != 0).sum())
+    assert halo_agents > 0  # some agents stood in the halos
