@@ -32,3 +32,25 @@ def test_warmup_below_three_is_refused():
                           "--steps", "2", "--warmup", "2"],
                          capture_output=True, text=True, timeout=120, cwd=ROOT)
     assert out.returncode != 0
+
+
+def test_traffic_figure_only_for_the_profiled_kernel_source(tmp_path, monkeypatch):
+    """roofline.traffic comes from the committed ncu summary only while the
+    summary's kernel-source hash matches the current kernel sources."""
+    sys.path.insert(0, ROOT)
+    import bench
+    cur = bench.kernel_source_hash()
+    f = tmp_path / "traffic.md"
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
+    f.write_text(f"kernel_source_sha256_16: {cur}\ndram_bytes_per_launch: 73932672\n")
+    assert bench.recorded_traffic() == 73932672.0
+    f.write_text("kernel_source_sha256_16: 0000000000000000\ndram_bytes_per_launch: 73932672\n")
+    assert bench.recorded_traffic() is None             # stale: taken on other sources
+    f.write_text(f"kernel_source_sha256_16: {cur}\n")
+    assert bench.recorded_traffic() is None             # no figure recorded
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "missing.md"))
+    assert bench.recorded_traffic() is None
+    # the committed summary names its own hash and figure
+    monkeypatch.undo()
+    text = open(bench.TRAFFIC_FILE).read()
+    assert "kernel_source_sha256_16:" in text and "dram_bytes_per_launch:" in text
